@@ -1,0 +1,397 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test names the passage or identity it checks.  None of them compares the
+oracle with itself: closed forms, library routines (numpy.fft, dense
+numpy.linalg solves/eigensolves), independent coefficient-space formulas,
+printed values and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.discretize import fourier_matrices, sine_matrix, kinetic_axis
+from oracle.unified import inner
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def paper_values():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, q, v, tol, _cite = [s.strip() for s in line.split("|")]
+        out[(name, q)] = (float(v), float(tol))
+    return out
+
+
+# ---------------------------------------------------------------- transforms
+
+@pytest.mark.parametrize("N", [8, 16, 64])
+def test_fourier_plane_wave_is_delta(N):
+    """Eq. fftp36: the coefficients of e^{2 pi i j p0/N} are delta_{p,p0}."""
+    fwd, inv, lam = fourier_matrices(N, 2.0)
+    j = np.arange(N)
+    for p0 in (-N // 2, -1, 0, 3, N // 2 - 1):
+        c = fwd @ np.exp(2j * math.pi * j * p0 / N)
+        e = np.zeros(N)
+        e[p0 + N // 2] = 1.0
+        assert np.max(np.abs(c - e)) < 1e-13
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_fourier_matches_numpy_fft(N):
+    """Eq. fftp36 is numpy's forward FFT / N with p reordered to -N/2..N/2-1."""
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    fwd, inv, _ = fourier_matrices(N, 1.0)
+    ref = np.fft.fftshift(np.fft.fft(f)) / N
+    assert np.max(np.abs(fwd @ f - ref)) < 1e-14
+    assert np.max(np.abs(inv @ (fwd @ f) - f)) < 1e-13
+
+
+@pytest.mark.parametrize("N", [8, 32, 64])
+def test_sine_involution_and_modes(N):
+    """Eq. tpll: C C = (N/2) I (DST-I), and sine modes map to deltas."""
+    C, lam = sine_matrix(N, 3.0)
+    assert np.max(np.abs(C @ C - (N / 2.0) * np.eye(N - 1))) < 1e-12
+    j = np.arange(1, N)
+    for l0 in (1, 2, N - 1):
+        coef = (2.0 / N) * C @ np.sin(j * l0 * math.pi / N)
+        e = np.zeros(N - 1)
+        e[l0 - 1] = 1.0
+        assert np.max(np.abs(coef - e)) < 1e-13
+    assert abs(lam[0] - math.pi / 3.0) < 1e-15
+
+
+def test_spectral_second_derivative_exact_on_modes():
+    """Eq. fftp35 / spdo1: -1/2 d_xx of a resolved plane wave / sine mode is exact."""
+    p = W.problem(1, (32,), (-3.0,), (5.0,), "fourier", is_complex=True)
+    g = O.build_grid(p)
+    x = g.nodes[0]
+    for q in (-15, -4, 1, 7, 15):
+        lam = 2 * math.pi * q / 8.0
+        f = np.exp(1j * lam * (x + 3.0))
+        assert np.max(np.abs(kinetic_axis(g, f, 0) - 0.5 * lam * lam * f)) < 1e-11
+    p = W.problem(1, (32,), (-3.0,), (5.0,), "sine")
+    g = O.build_grid(p)
+    x = g.nodes[0]
+    for l in (1, 5, 31):
+        lam = math.pi * l / 8.0
+        f = np.sin(lam * (x + 3.0))
+        assert np.max(np.abs(kinetic_axis(g, f, 0) - 0.5 * lam * lam * f)) < 1e-11
+
+
+# ---------------------------------------------------------------- operator
+
+@pytest.mark.parametrize("disc", ["fourier", "sine"])
+def test_harmonic_ground_state_closed_form(disc):
+    """beta = 0, Omega = 0, Eq. harmpen: prod (g/pi)^{1/4} e^{-g x^2/2} is an
+    eigenfunction with eigenvalue sum g/2; spectral grids reach ~1e-13."""
+    gam = (1.0, 2.0, 1.5)
+    p = W.problem(3, (48, 64, 48), (-8.0,) * 3, (8.0,) * 3, disc,
+                  potential={"kind": "harmonic", "gamma": gam})
+    g = O.build_grid(p)
+    f = np.ones(g.shape)
+    for a in range(3):
+        f = f * np.exp(-0.5 * gam[a] * g.mesh(a) ** 2)
+    lam = sum(gam) / 2.0
+    r = O.apply_hlin(g, f) - lam * f
+    assert np.max(np.abs(r)) < 1e-10
+    f = f / math.sqrt(O.norm2(g, f))
+    assert abs(O.energy(g, f) - lam) < 1e-10
+
+
+def test_rotation_sign_from_lz_eigenfunctions():
+    """-Omega L_z with L_z = -i(x d_y - y d_x) (Eq. GPE): (x +- iy) e^{-r^2/2}
+    has L_z = +-1, so its energy at beta = 0 is 2 -+ Omega; the isotropic
+    Gaussian has L_z = 0 and energy 1."""
+    om = 0.7
+    p = W.problem(2, (64, 64), (-10.0, -10.0), (10.0, 10.0), "fourier", omega=om, is_complex=True)
+    g = O.build_grid(p)
+    x, y = g.mesh(0), g.mesh(1)
+    pa = np.broadcast_to(np.exp(-(x * x + y * y) / 2) + 0j, g.shape)
+    for f, lam in ((pa, 1.0), ((x + 1j * y) * pa, 2.0 - om), ((x - 1j * y) * pa, 2.0 + om)):
+        assert np.max(np.abs(O.apply_hlin(g, f) - lam * f)) < 1e-12
+        f = f / math.sqrt(O.norm2(g, f))
+        assert abs(O.energy(g, f) - lam) < 1e-12
+
+
+def test_fd_second_order():
+    """§2.1: the FD operator is second-order accurate (error ratio ~4 per halving)."""
+    errs = []
+    for N in (64, 128, 256):
+        p = W.problem(1, (N,), (-10.0,), (10.0,), "fd")
+        g = O.build_grid(p)
+        f = np.exp(-g.mesh(0) ** 2 / 2)
+        errs.append(np.max(np.abs(O.apply_hlin(g, f) - 0.5 * f)))
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4
+
+
+def test_fd_matrix_is_paper_tridiagonal():
+    """§2.1: A has a_jj = 1/h^2 + V(x_j), a_j,j+-1 = -1/(2h^2); E_h = h[Phi^T A Phi + beta/2 sum phi^4]."""
+    p = W.problem(1, (10,), (-2.0,), (3.0,), "fd", beta=3.0)
+    g = O.build_grid(p)
+    h = g.h[0]
+    M = 9
+    A = np.diag(1.0 / h ** 2 + g.V) - np.diag(np.full(M - 1, 0.5 / h ** 2), 1) \
+        - np.diag(np.full(M - 1, 0.5 / h ** 2), -1)
+    rng = np.random.default_rng(2)
+    phi = rng.standard_normal(M)
+    assert np.max(np.abs(O.apply_hlin(g, phi) - A @ phi)) < 1e-12
+    E = h * (phi @ A @ phi + 1.5 * np.sum(phi ** 4))
+    assert abs(O.energy(g, phi) - E) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["fourier2d_rot", "fourier3d", "sine2d"])
+def test_energy_parseval_forms(case):
+    """E_h via Eq. energy-discrete-FP (coefficients, rotation folded per line) or
+    Eq. BCD equals h_vol sum conj(psi) H psi + beta/2|psi|^4 on random data."""
+    rng = np.random.default_rng(3)
+    if case == "fourier2d_rot":
+        p = W.problem(2, (16, 32), (-4.0, -5.0), (4.0, 6.0), "fourier", beta=7.0, omega=0.6,
+                      is_complex=True)
+    elif case == "fourier3d":
+        p = W.problem(3, (8, 16, 8), (-4.0,) * 3, (4.0,) * 3, "fourier", beta=3.0)
+    else:
+        p = W.problem(2, (16, 12), (-4.0, -3.0), (4.0, 5.0), "sine", beta=5.0,
+                      potential={"kind": "lattice", "gamma": (1.0, 1.0), "depth": 10.0, "k": 0.7})
+    g = O.build_grid(p)
+    psi = rng.standard_normal(g.shape)
+    if g.is_complex:
+        psi = psi + 1j * rng.standard_normal(g.shape)
+    assert abs(O.energy(g, psi) - O.energy_parseval(g, psi)) < 1e-10 * abs(O.energy(g, psi))
+
+
+def test_hermitian_operator():
+    """A is Hermitian (Eq. prob): <u, H v> = conj<v, H u> on random complex data."""
+    rng = np.random.default_rng(4)
+    p = W.problem(2, (16, 16), (-4.0, -4.0), (4.0, 4.0), "fourier", omega=0.9, is_complex=True)
+    g = O.build_grid(p)
+    u = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    v = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    a = np.vdot(u, O.apply_hlin(g, v))
+    b = np.conj(np.vdot(v, O.apply_hlin(g, u)))
+    assert abs(a - b) < 1e-10 * abs(a)
+
+
+# ---------------------------------------------------------------- unified problem
+
+def _unified_case(omega=0.5, beta=30.0):
+    p = W.problem(2, (8, 8), (-3.0, -3.0), (3.0, 3.0), "fourier", beta=beta, omega=omega,
+                  is_complex=True)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    X /= np.linalg.norm(X)
+    D = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    return g, U, X, D
+
+
+def test_rescaling_matches_energy():
+    """Reading of 'a proper rescaling' (§3): F(sqrt(h) psi) = E_h(psi), theta = 2 mu."""
+    p = W.config("c1")
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    psi = W.gaussian(p)
+    X = U.to_X(psi)
+    F, G = U.fg(X)
+    assert abs(F - O.energy(g, psi)) < 1e-12 * F
+    assert abs(inner(X, G) - 2 * O.chem_potential(g, psi)) < 1e-11 * F
+
+
+def test_gradient_and_hessian_vs_finite_differences():
+    """Lemma 3.1: directional derivatives agree with central differences of F
+    and of the gradient (truncation O(eps^2))."""
+    g, U, X, D = _unified_case()
+    eps = 1e-5
+    fd1 = (U.F(X + eps * D) - U.F(X - eps * D)) / (2 * eps)
+    G = U.grad(X)
+    assert abs(fd1 - inner(D, G)) < 1e-6 * max(1.0, abs(fd1))
+    fd2 = (U.grad(X + eps * D) - U.grad(X - eps * D)) / (2 * eps)
+    HD = U.hessvec(X, D)
+    assert np.max(np.abs(fd2 - HD)) < 1e-5 * np.max(np.abs(HD))
+    assert abs(inner(D, HD) - U.hess_quad(X, D)) < 1e-10 * abs(inner(D, HD))
+
+
+def test_homogeneity_identities():
+    """F = F2 + F4 with F2 quadratic, F4 quartic: Re<X,G> = X*AX + 4 alpha sum|X|^4
+    and Re<X,H[X]> = X*AX + 12 alpha sum|X|^4 (Euler's theorem)."""
+    g, U, X, _ = _unified_case()
+    xax = inner(X, U.A(X))
+    s4 = float(np.sum(np.abs(X) ** 4))
+    assert abs(inner(X, U.grad(X)) - (xax + 4 * U.alpha * s4)) < 1e-10 * abs(xax)
+    assert abs(inner(X, U.hessvec(X, X)) - (xax + 12 * U.alpha * s4)) < 1e-10 * abs(xax)
+
+
+def test_phase_invariance_kernel():
+    """F(e^{it}X) = F(X): the gradient is orthogonal to iX, and H[iX] = i G - ...:
+    the derivative of G(e^{it}X) at t=0 is i G, so H[iX] = i G."""
+    g, U, X, _ = _unified_case()
+    G = U.grad(X)
+    assert abs(inner(1j * X, G)) < 1e-10 * np.linalg.norm(G)
+    assert np.max(np.abs(U.hessvec(X, 1j * X) - 1j * G)) < 1e-10 * np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_cayley_closed_form_vs_dense_solve(cplx):
+    """Theorem 3.3 equals the solution of Eq. eq-Y by a dense linear solve, and
+    preserves the norm; Y(0) = X; Y'(0) = -2 A(X)X."""
+    omega = 0.5 if cplx else 0.0
+    p = W.problem(1, (12,), (-3.0,), (3.0,), "fourier", beta=20.0, omega=0.0, is_complex=cplx)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal(g.shape) + (1j * rng.standard_normal(g.shape) if cplx else 0)
+    X /= np.linalg.norm(X)
+    G = U.grad(X)
+    for tau in (0.0, 1e-3, 0.05, 0.7):
+        Y = O.cayley_step(X, G, tau)
+        Yd = O.cayley_dense(X, G, tau)
+        assert np.max(np.abs(Y - Yd)) < 1e-12
+        assert abs(np.linalg.norm(Y) - 1.0) < 1e-13
+    t = 1e-6
+    dY = (O.cayley_step(X, G, t) - O.cayley_step(X, G, -t)) / (2 * t)
+    assert np.max(np.abs(dY + 2 * O.proj_grad(X, G))) < 1e-6 * np.max(np.abs(G))
+    del omega
+
+
+def test_ratio_model_second_order():
+    """§3.2: the RN model is F's second-order expansion, so
+    |ared - (pred - delta/2 ||D||^2)| = O(||D||^3) and rho -> 1 as D -> 0."""
+    g, U, X, D = _unified_case()
+    G = U.grad(X)
+    F0 = U.F(X)
+    errs = []
+    for s in (1e-2, 5e-3, 2.5e-3):
+        Dd = s * D
+        ared = U.F(X + Dd) - F0
+        model = inner(G, Dd) + 0.5 * U.hess_quad(X, Dd)
+        errs.append(abs(ared - model))
+    assert 6.0 < errs[0] / errs[1] < 10.0 and 6.0 < errs[1] / errs[2] < 10.0
+
+
+# ---------------------------------------------------------------- solvers
+
+def test_fg_tiny_grid_reaches_dense_eigenvalue():
+    """beta = 0: min of F on the sphere is the smallest eigenvalue of A/2 = H_lin,
+    here from numpy.linalg.eigh of the explicit matrix (library routine)."""
+    p = W.problem(2, (8, 8), (-4.0, -4.0), (4.0, 4.0), "fourier", beta=0.0, omega=0.4,
+                  is_complex=True, potential={"kind": "harmonic", "gamma": (1.0, 1.3)})
+    g = O.build_grid(p)
+    M = 64
+    H = np.zeros((M, M), complex)
+    for k in range(M):
+        e = np.zeros(M, complex)
+        e[k] = 1.0
+        H[:, k] = O.apply_hlin(g, e.reshape(g.shape)).ravel()
+    lam_min = np.linalg.eigvalsh(0.5 * (H + H.conj().T))[0]
+    U = O.Unified(g)
+    rng = np.random.default_rng(7)
+    X0 = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    X0 /= np.linalg.norm(X0)
+    r = O.feasible_gradient(U.fg, X0, max_iter=5000, eps0=0.0, res_tol=1e-11)
+    assert abs(r.F - lam_min) < 1e-10
+    r2 = O.regularized_newton(U, X0, res_tol=1e-11)
+    assert abs(r2.F - lam_min) < 1e-10
+
+
+def test_paper_1d_values_case1_and_case2():
+    """§4.1: printed E_g, mu_g, x_rms for Case I (Fourier 512, our C1 grid) and
+    Case II (sine, h = 1/8)."""
+    pv = paper_values()
+    for name in ("c1", "1d_case2"):
+        p = W.config(name)
+        g = O.build_grid(p)
+        U = O.Unified(g)
+        r = O.feasible_gradient(U.fg, U.to_X(W.gaussian(p)), max_iter=5000, eps0=1e-12)
+        psi = U.to_psi(r.X)
+        got = {"E": O.energy(g, psi), "mu": O.chem_potential(g, psi), "xrms": O.rms(g, psi, 0)}
+        for q, val in got.items():
+            ref, tol = pv[(name, q)]
+            assert abs(val - ref) <= tol, (name, q, val, ref)
+
+
+def test_paper_c2_value_and_virial_and_tf():
+    """§4.3 Table 9 (Omega = 0, beta = 1000): E = 11.9718 via Algorithm 3 + 2.
+    Virial identity for harmonic traps (textbook): 2 E_kin - 2 E_pot + d E_int = 0.
+    Thomas-Fermi limit: E -> (d+2)/(d+4) mu_TF, mu_TF = (beta/pi)^{1/2} in 2D."""
+    pv = paper_values()
+    p = W.config("c2")
+    g, psi, res = O.cascadic(p, W.gaussian(p), levels=3, method="rn", res_tol_psi=1e-10)
+    E = O.energy(g, psi)
+    ref, tol = pv[("c2", "E")]
+    assert abs(E - ref) <= tol
+    a2 = np.abs(psi) ** 2
+    from oracle.discretize import apply_kinetic
+    ekin = g.h_vol * float(np.sum(np.real(np.conj(psi) * apply_kinetic(g, psi))))
+    epot = g.h_vol * float(np.sum(g.V * a2))
+    eint = g.h_vol * 0.5 * g.beta * float(np.sum(a2 * a2))
+    assert abs(2 * ekin - 2 * epot + 2 * eint) < 1e-6 * E
+    mu_tf = math.sqrt(g.beta / math.pi)
+    assert abs(E - (4.0 / 6.0) * mu_tf) < 0.02 * E
+
+
+def test_tf_limit_1d():
+    """1D Thomas-Fermi: mu_TF = 1/2 (3 beta/2)^{2/3}, E_TF = 3/5 mu_TF (Eq. TFA)."""
+    p = W.config("c1")
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    r = O.feasible_gradient(U.fg, U.to_X(W.gaussian(p)), max_iter=3000, eps0=1e-10)
+    mu_tf = 0.5 * (1.5 * 400.0) ** (2.0 / 3.0)
+    assert abs(r.F - 0.6 * mu_tf) < 0.01 * r.F
+
+
+def test_rn_result_independent_of_delta0():
+    """§3.2 says results are insensitive to the RN parameters: the final E is
+    the same for delta0 = 1e-2, 1, 100."""
+    p = W.problem(1, (128,), (-12.0,), (12.0,), "fourier", beta=100.0)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    X0 = U.to_X(W.gaussian(p))
+    Es = [O.regularized_newton(U, X0, delta0=d, k_init=20, res_tol=1e-11).F for d in (1e-2, 1.0, 100.0)]
+    assert max(Es) - min(Es) < 1e-11 * Es[0]
+
+
+# ---------------------------------------------------------------- prolongation
+
+@pytest.mark.parametrize("disc", ["fourier", "sine"])
+def test_prolongation_exact_on_band_limited_and_injects(disc):
+    """Algorithm 3 transfer (reading: spectral zero-padding): a function resolved
+    on the coarse grid is reproduced exactly on the fine grid; restricting back
+    to the coarse nodes gives the coarse values (injection)."""
+    Nc = 16
+    L = 6.0
+    pc = W.problem(2, (Nc, Nc), (-3.0, -3.0), (3.0, 3.0), disc)
+    pf = W.problem(2, (2 * Nc, 2 * Nc), (-3.0, -3.0), (3.0, 3.0), disc)
+    gc, gf = O.build_grid(pc), O.build_grid(pf)
+
+    def f(g):
+        x, y = g.mesh(0) + 3.0, g.mesh(1) + 3.0
+        if disc == "fourier":
+            return np.cos(2 * math.pi * 3 * x / L) * np.sin(2 * math.pi * 5 * y / L) + 0.3 * np.cos(2 * math.pi * 7 * x / L)
+        return np.sin(math.pi * 2 * x / L) * np.sin(math.pi * 13 * y / L) + 0.5 * np.sin(math.pi * 15 * x / L) * np.sin(math.pi * y / L)
+    fc = f(gc)
+    ff = f(gf)
+    pro = O.prolong(gc, gf, fc)
+    scale = math.sqrt(O.norm2(gf, ff))
+    assert np.max(np.abs(pro * scale - ff)) < 1e-12
+    inj = O.inject(gf, gc, pro * scale)
+    assert np.max(np.abs(inj - fc)) < 1e-12
+
+
+def test_fd_prolongation_linear_exact():
+    """FD transfer (reading: linear interpolation) reproduces piecewise-linear data."""
+    pc = W.problem(1, (8,), (0.0,), (8.0,), "fd")
+    pf = W.problem(1, (16,), (0.0,), (8.0,), "fd")
+    gc, gf = O.build_grid(pc), O.build_grid(pf)
+    tent = lambda x: np.minimum(x, 8.0 - x)
+    pro = O.prolong(gc, gf, tent(gc.nodes[0]))
+    ff = tent(gf.nodes[0])
+    assert np.max(np.abs(pro * math.sqrt(O.norm2(gf, ff)) - ff)) < 1e-12

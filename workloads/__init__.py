@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs for the Gross-Pitaevskii ground-state workloads.
+
+This module is shared by the tests, ``bench.py`` and ``__graft_entry__``.  It
+holds problem *parameters* (grids, traps, beta, Omega) and *initial data*
+sampled on the grid.  It contains none of the method's arithmetic: no
+transform, no operator, no energy, no optimisation step.  Both the FP64 CPU
+oracle and the CUDA library read the parameter dictionaries below and each
+builds its own grid, potential and operator from them.
+
+Grid convention (paper §2):
+  * Fourier pseudospectral ("fourier"): N points per axis, x_j = a + j h,
+    j = 0..N-1, h = (b-a)/N (periodic).
+  * Sine pseudospectral ("sine") and finite difference ("fd"): N intervals,
+    N-1 interior unknowns x_j = a + j h, j = 1..N-1 (homogeneous Dirichlet).
+Arrays are C-ordered with x fastest: shape (n_x,), (n_y, n_x) or
+(n_z, n_y, n_x).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "problem", "axis_nodes", "array_shape", "cell_volume", "normalise",
+    "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep",
+]
+
+
+def problem(dim, n, lo, hi, disc="fourier", beta=0.0, omega=0.0,
+            potential=None, is_complex=None):
+    """Parameter dictionary for one ground-state problem.
+
+    ``n`` is the paper's N per axis (points for Fourier, intervals for sine
+    and FD).  ``potential`` is one of
+      {"kind": "harmonic", "gamma": (gx, gy, gz)}                 (Eq. harmpen)
+      {"kind": "lattice", "gamma": (...), "depth": A, "k": k}     V = harmonic + A*sum sin^2(k x)
+      {"kind": "stirrer", "gamma": (...), "w0":, "delta":, "r0":}  (§4.2 Case II)
+    """
+    n = tuple(int(v) for v in n)
+    lo = tuple(float(v) for v in lo)
+    hi = tuple(float(v) for v in hi)
+    assert len(n) == dim and len(lo) == dim and len(hi) == dim
+    if potential is None:
+        potential = {"kind": "harmonic", "gamma": (1.0,) * dim}
+    pot = dict(potential)
+    g = tuple(float(v) for v in pot.get("gamma", (1.0,) * dim))
+    pot["gamma"] = g + (1.0,) * (3 - len(g))
+    if is_complex is None:
+        is_complex = omega != 0.0
+    return {"dim": dim, "n": n, "lo": lo, "hi": hi, "disc": disc,
+            "beta": float(beta), "omega": float(omega), "potential": pot,
+            "is_complex": bool(is_complex)}
+
+
+def axis_nodes(p, axis):
+    """Coordinates of the unknowns along one axis (x = axis 0)."""
+    n, a, b = p["n"][axis], p["lo"][axis], p["hi"][axis]
+    h = (b - a) / n
+    if p["disc"] == "fourier":
+        j = np.arange(n, dtype=np.float64)
+    else:
+        j = np.arange(1, n, dtype=np.float64)
+    return a + j * h
+
+
+def array_shape(p):
+    """Numpy shape of a grid function, x fastest (last)."""
+    ext = [len(axis_nodes(p, a)) for a in range(p["dim"])]
+    return tuple(reversed(ext))
+
+
+def cell_volume(p):
+    return float(np.prod([(p["hi"][a] - p["lo"][a]) / p["n"][a] for a in range(p["dim"])]))
+
+
+def _mesh(p):
+    """Coordinate arrays broadcast to the array shape, ordered (x, y, z)."""
+    d = p["dim"]
+    axes = [axis_nodes(p, a) for a in range(d)]
+    out = []
+    for a in range(d):
+        shape = [1] * d
+        shape[d - 1 - a] = len(axes[a])
+        out.append(axes[a].reshape(shape))
+    return out
+
+
+def normalise(p, psi):
+    """Scale so that h_vol * sum |psi|^2 = 1 (discrete constraint)."""
+    nrm = math.sqrt(cell_volume(p) * float(np.sum(np.abs(psi) ** 2)))
+    return psi / nrm
+
+
+def gaussian(p, dtype=np.float64):
+    """Normalised Gaussian prod_i exp(-gamma_i x_i^2 / 2) sampled on the grid."""
+    xs = _mesh(p)
+    g = p["potential"]["gamma"]
+    psi = np.ones(array_shape(p), dtype=np.float64)
+    for a, x in enumerate(xs):
+        psi = psi * np.exp(-0.5 * g[a] * x * x)
+    psi = normalise(p, psi)
+    if p["is_complex"]:
+        psi = psi.astype(np.complex128)
+    return psi.astype(dtype) if dtype is not None else psi
+
+
+def rotating_initial(p, kind="c", noise=0.0, seed=1504):
+    """Initial data (a), (b), (b-bar), (c), (c-bar), (d), (d-bar) of §4.3.
+
+    phi_a = exp(-(x^2+y^2)/2)/sqrt(pi), phi_b = (x+iy) phi_a; (c) is the
+    normalised mean of (a) and (b); (d) mixes them with weights (1-Omega) and
+    Omega.  A bar conjugates.  ``noise`` > 0 multiplies by exp(i*noise*xi),
+    xi iid standard normal from numpy default_rng(seed) in C order, then
+    renormalises.
+    """
+    x, y = _mesh(p)[:2]
+    pa = np.exp(-(x * x + y * y) / 2.0) / math.sqrt(math.pi) + 0j
+    pa = np.broadcast_to(pa, array_shape(p)).astype(np.complex128)
+    pb = (x + 1j * y) * pa
+    base = kind.split("_")[0]
+    conj = kind.endswith("_bar")
+    if base == "a":
+        psi = pa
+    elif base == "b":
+        psi = pb
+    elif base == "c":
+        psi = (pa + pb) / 2.0
+    elif base == "d":
+        om = p["omega"]
+        psi = (1.0 - om) * pa + om * pb
+    else:
+        raise ValueError(kind)
+    if conj:
+        psi = np.conj(psi)
+    if noise > 0.0:
+        xi = np.random.default_rng(seed).standard_normal(array_shape(p))
+        psi = psi * np.exp(1j * noise * xi)
+    return normalise(p, psi)
+
+
+_LATTICE_K = math.pi / 4.0
+
+
+def config(name):
+    """The named workloads (parameters only)."""
+    if name == "c1":      # 1D, Fourier 512, harmonic, beta=400
+        return problem(1, (512,), (-16.0,), (16.0,), "fourier", beta=400.0)
+    if name == "c2":      # 2D, Fourier 256^2, harmonic, beta=1000, cascade 64->128->256
+        return problem(2, (256, 256), (-16.0, -16.0), (16.0, 16.0), "fourier", beta=1000.0)
+    if name == "c3":      # 3D sine 128^3, harmonic + depth-100 lattice, beta=1600
+        return problem(3, (128,) * 3, (-8.0,) * 3, (8.0,) * 3, "sine", beta=1600.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0, 1.0),
+                                  "depth": 100.0, "k": _LATTICE_K})
+    if name == "c3p":     # Table 5 validation: depth 50, beta=800
+        return problem(3, (128,) * 3, (-8.0,) * 3, (8.0,) * 3, "sine", beta=800.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0, 1.0),
+                                  "depth": 50.0, "k": _LATTICE_K})
+    if name == "c4":      # 2D rotating, Fourier 512^2, Omega=0.9, beta=1000
+        return problem(2, (512, 512), (-16.0, -16.0), (16.0, 16.0), "fourier",
+                       beta=1000.0, omega=0.9, is_complex=True)
+    if name == "1d_case2":  # §4.1 Case II (sine): V = x^2/2 + 25 sin^2(pi x/4), beta=250
+        return problem(1, (256,), (-16.0,), (16.0,), "sine", beta=250.0,
+                       potential={"kind": "lattice", "gamma": (1.0,), "depth": 25.0,
+                                  "k": _LATTICE_K})
+    raise KeyError(name)
+
+
+CONFIGS = ("c1", "c2", "c3", "c3p", "c4", "1d_case2")
+
+
+def batched_sweep(count=256, seed=20150410):
+    """The batched-sweep instance list: grids from {64,128,256}^2 on [-12,12]^2,
+    beta ~ U[100,1000], Omega ~ U[0,0.9], gamma_y ~ U[1,1.2], gamma_x = 1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([64, 128, 256]))
+        beta = float(rng.uniform(100.0, 1000.0))
+        om = float(rng.uniform(0.0, 0.9))
+        gy = float(rng.uniform(1.0, 1.2))
+        out.append(problem(2, (n, n), (-12.0, -12.0), (12.0, 12.0), "fourier",
+                           beta=beta, omega=om, is_complex=True,
+                           potential={"kind": "harmonic", "gamma": (1.0, gy)}))
+    return out
