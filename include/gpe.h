@@ -1,0 +1,185 @@
+/*
+ * gpe.h -- C ABI of libgpe: GB300 (sm_103a) kernels for the regularized Newton
+ * ground-state method of Wu, Wen & Bao, "A Regularized Newton Method for
+ * Computing Ground States of Bose-Einstein Condensates" (arXiv:1504.02891).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grids (paper §2).  For GPE_FOURIER, n[a] is the number of periodic points N_a
+ * on [lo, hi) with x_j = lo + j h, h = (hi-lo)/N_a, j = 0..N_a-1 (§2.3).  For
+ * GPE_SINE and GPE_FD, n[a] is the number of intervals N_a and the unknowns are
+ * the N_a - 1 interior nodes x_j = lo + j h, j = 1..N_a-1 (§2.1, §2.2).
+ *
+ * Layout.  A grid function ("psi buffer") is a DEVICE array, row-major
+ * [batch][nz][ny][nx] with x fastest, of the plan's precision: float/double when
+ * the plan is real (is_complex = 0), interleaved complex float2/double2 when it
+ * is complex.  Values are physical grid values psi_j with the discrete norm
+ * ||psi||_h^2 = h_vol * sum |psi_j|^2, h_vol = prod h_a.
+ *
+ * Units.  E and mu are the paper's E_h and mu_h (Eq. energy-discrete-FD,
+ * energy-discrete-SP-34, energy-discrete-FP, chemical-potential).  H psi is
+ * (-1/2 Delta_h + V + beta |psi|^2 - Omega L_z,h) psi, so the paper's gradient
+ * G_h = nabla E_h equals 2 h_vol H psi.
+ *
+ * Ownership.  The caller owns every psi/direction/output buffer and keeps it
+ * alive until the work queued on the plan's stream has finished.  The plan owns
+ * its tables (potential, symbols, twiddles), workspace and reduction scratch.
+ *
+ * Execution.  Work is queued on the CUDA stream given at plan creation (NULL:
+ * the legacy default stream).  Entry points that return host scalars
+ * synchronise that stream; the others are asynchronous.  Buffers must not
+ * alias unless an entry point says so.
+ *
+ * Errors.  Every call returns a gpe_status; nothing aborts or throws across the
+ * ABI.  gpe_last_error() returns a message for the last failure on the calling
+ * thread.  Invalid arguments return GPE_EINVAL before any work is queued.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpe_plan_s* gpe_plan;
+
+typedef enum {
+  GPE_OK = 0,
+  GPE_EINVAL = 1,      /* bad argument (shape, pointer, option)                */
+  GPE_ECUDA = 2,       /* a CUDA runtime call failed                            */
+  GPE_ENOMEM = 3,      /* device allocation failed                              */
+  GPE_ENONFINITE = 4,  /* a reduction produced NaN/Inf                          */
+  GPE_ENOCONV = 5,     /* iteration cap reached; outputs are still written      */
+  GPE_ETIMEOUT = 6     /* a bounded device wait expired                         */
+} gpe_status;
+
+typedef enum { GPE_FOURIER = 0, GPE_SINE = 1, GPE_FD = 2 } gpe_disc;
+typedef enum { GPE_F32 = 0, GPE_F64 = 1 } gpe_prec;
+
+/* External trap V (Eq. harmpen, optic98/asypon, §4.2 Case II):
+ *   GPE_V_HARMONIC: V = 1/2 sum_a g_a^2 x_a^2,           v_param[0..2] = g_x, g_y, g_z
+ *   GPE_V_LATTICE : harmonic + A sum_a sin^2(k x_a),      v_param[3] = A, v_param[4] = k
+ *   GPE_V_STIRRER : harmonic + w0 exp(-d((x-r0)^2+y^2)),  v_param[3] = w0, [4] = d, [5] = r0
+ *   GPE_V_ARRAY   : v_host points to the potential on the grid (host, float64,
+ *                   one instance's unknowns in the layout above); copied.      */
+typedef enum { GPE_V_HARMONIC = 0, GPE_V_LATTICE = 1, GPE_V_STIRRER = 2, GPE_V_ARRAY = 3 } gpe_vkind;
+
+typedef struct {
+  int dim;               /* 1, 2 or 3                                           */
+  int n[3];              /* N_a per axis (see Grids); unused axes ignored       */
+  double lo[3], hi[3];   /* computational box U                                 */
+  int disc;              /* gpe_disc                                            */
+  double beta;           /* interaction constant                                */
+  double omega;          /* rotation speed; nonzero needs is_complex, dim >= 2,
+                            and GPE_FOURIER or GPE_FD (§2.2 uses sine for
+                            Omega = 0 only)                                      */
+  int is_complex;        /* 0: real psi (Omega = 0), 1: complex psi             */
+  int v_kind;            /* gpe_vkind                                           */
+  double v_param[8];
+  const double* v_host;  /* GPE_V_ARRAY only                                    */
+} gpe_problem;
+
+/* Create a plan for `nbatch` >= 1 instances of problem *p on one device.
+ * Fourier grids need every n[a] to be a power of two in [4, 1024]; sine grids
+ * need n[a] a power of two in [4, 512] (the DST-I runs as a 2N-point FFT of
+ * the odd extension); FD grids need n[a] >= 3.  prec is gpe_prec.  stream is
+ * a cudaStream_t (may be NULL).  On success *out receives the plan.
+ * Errors: GPE_EINVAL (shape/option), GPE_ENOMEM, GPE_ECUDA. */
+gpe_status gpe_plan_create(const gpe_problem* p, int nbatch, int prec, void* stream,
+                           gpe_plan* out);
+
+/* Release the plan and everything it owns (synchronises its stream). */
+gpe_status gpe_plan_destroy(gpe_plan plan);
+
+/* Text of the last failure on this thread ("" if none).  Never NULL. */
+const char* gpe_last_error(void);
+
+/* Number of unknowns of one instance and the cell volume h_vol. */
+gpe_status gpe_plan_size(gpe_plan plan, int64_t* n_unknowns, double* h_vol);
+
+/* Discrete energy of each instance: E[b] = E_h(psi_b), mu[b] = mu_h(psi_b),
+ * norm2[b] = ||psi_b||_h^2 (Eq. energy-discrete-*, chemical-potential, §2).
+ * Each output is a host array of nbatch doubles, or NULL.  Synchronises.
+ * Reductions are accumulated in float64 whatever the plan precision. */
+gpe_status gpe_energy(gpe_plan plan, const void* psi, double* E, double* mu, double* norm2);
+
+/* hpsi = H(psi) psi = (-1/2 Delta_h + V + beta|psi|^2 - Omega L_z,h) psi, i.e.
+ * G_h / (2 h_vol) with G_h of Eq. Gh1dsin and its Fourier/FD analogues.  If E or
+ * mu is non-NULL it also returns E_h and mu_h per instance (host arrays;
+ * synchronises); otherwise the call is asynchronous.  hpsi must not alias psi. */
+gpe_status gpe_grad(gpe_plan plan, const void* psi, void* hpsi, double* E, double* mu);
+
+/* out = H_psi[d] + shift * d, the Hessian of Lemma 3.1 in grid units:
+ * H_psi[d] = (-1/2 Delta_h + V - Omega L_z,h) d + beta (|psi|^2 d + 2 Re(conj(psi) d) psi).
+ * In the unified variables X = sqrt(h_vol) psi of Eq. prob this is
+ * nabla^2 F(X)[D] / 2.  Asynchronous.  out must not alias psi or d. */
+gpe_status gpe_hessvec(gpe_plan plan, const void* psi, const void* d, double shift, void* out);
+
+/* One sphere-preserving Cayley step (Eq. eq-Y, Theorem 3.3) in the unified
+ * variables X = sqrt(h_vol) psi, G = 2 sqrt(h_vol) hpsi, for every instance:
+ *   Y(tau) = a(tau) X + b(tau) G, then scaled to ||Y||_2 = 1 (the §4
+ *   renormalisation), written back in grid units to psi_out.
+ * psi must satisfy ||psi||_h ~ 1 and hpsi must be H(psi) psi (gpe_grad).
+ * tau >= 0 is the step of Theorem 3.3 in the unified variables.  If E_out is
+ * non-NULL, E_h(psi_out) per instance is returned (synchronises).
+ * psi_out must not alias psi or hpsi. */
+gpe_status gpe_feasible_step(gpe_plan plan, const void* psi, const void* hpsi, double tau,
+                             void* psi_out, double* E_out);
+
+/* Cascadic transfer (Algorithm 3): interpolate psi_c from the coarse plan's
+ * grid to the fine plan's grid and renormalise to ||psi_f||_h = 1.  Both plans
+ * must have the same dim, box, discretisation, complexity, batch and precision,
+ * and fine->n[a] = 2 * coarse->n[a].  Fourier: zero-padding of the centred
+ * spectrum with the Nyquist coefficient split evenly; sine: zero-padding of the
+ * DST-I coefficients; FD: linear interpolation.  Runs on the fine plan's stream. */
+gpe_status gpe_prolong(gpe_plan coarse, gpe_plan fine, const void* psi_c, void* psi_f);
+
+/* Options of gpe_rnewton_solve.  gpe_solve_opts_default() fills the values
+ * given in brackets. */
+typedef struct {
+  int levels;         /* cascade levels of Algorithm 3, >= 1 (coarsest = n >> (levels-1)) [1] */
+  int mode;           /* 0: float64 throughout; 1: float32 bulk then float64
+                         refinement; 2: float32 only                           [1] */
+  int method;         /* 0: Algorithm 2 (regularized Newton); 1: Algorithm 1    [0] */
+  int k_init;         /* Algorithm 1 warm-start iterations in Algorithm 2       [100] */
+  int k_sub;          /* Algorithm 1 iterations per subproblem (Eq. tr-sub)     [200] */
+  int max_outer;      /* regularized Newton iterations per level and precision  [200] */
+  int max_iter;       /* Algorithm 1 iterations when method = 1                 [2000] */
+  double eps0;        /* Eq. crit1 tolerance (Algorithm 1)                      [1e-6] */
+  double delta_stop;  /* Eq. crit2 tolerance on accepted steps (Algorithm 2)    [1e-8] */
+  double res_tol;     /* stop when ||H psi - mu psi||_h <= res_tol (0 = off)    [1e-9] */
+  double delta0;      /* initial regularisation (unified variables)             [1.0] */
+  double switch_rel;  /* mode 1: leave float32 once ||H psi - mu psi||_h <=
+                         switch_rel * mu or float32 stagnates                   [2e-6] */
+  int chunk;          /* Algorithm 1 iterations queued between host checks      [16] */
+  int use_graphs;     /* capture the queued iterations in CUDA graphs           [1] */
+} gpe_solve_opts;
+
+typedef struct {
+  double E, mu;       /* E_h, mu_h of the result (float64 evaluation)           */
+  double res;         /* ||H psi - mu psi||_h of the result                     */
+  int status;         /* gpe_status of the solve                               */
+  int outer_f32, outer_f64;   /* regularized Newton iterations on the finest level */
+  int inner_f32, inner_f64;   /* Algorithm 1 iterations on the finest level         */
+  int nfe;                    /* operator applications, all levels              */
+  double ms_f32, ms_f64;      /* wall time of the float32 / float64 phases       */
+} gpe_solve_report;
+
+gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
+
+/* Ground state by Algorithm 3 (cascade) around Algorithm 2 (or 1), for a plan
+ * with nbatch = 1.  psi_inout holds the initial guess on the plan's (finest)
+ * grid; the coarsest level starts from its values at the coarse nodes
+ * (injection), normalised.  On return psi_inout holds the computed state,
+ * normalised, in the plan's precision.  report may be NULL.  Synchronises.
+ * Returns GPE_ENOCONV if an iteration cap ended the finest level before the
+ * stopping rules (the state is still written). */
+gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
+                             gpe_solve_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPE_H */

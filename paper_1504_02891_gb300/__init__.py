@@ -1,0 +1,289 @@
+"""Python binding of libgpe: the regularized Newton ground-state method of
+Wu, Wen & Bao (arXiv:1504.02891) on GB300 (sm_103a).
+
+Argument marshalling only: every step runs in the CUDA library behind the C
+ABI declared in include/gpe.h.  Device buffers are passed as torch CUDA
+tensors (their data pointers); torch is used for device memory and streams.
+Importing this package loads ``libgpe.so`` and fails loudly if it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+__all__ = ["lib", "Problem", "Plan", "SolveOpts", "SolveReport", "GPEError",
+           "FOURIER", "SINE", "FD", "F32", "F64", "load", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgpe.so")
+
+FOURIER, SINE, FD = 0, 1, 2
+F32, F64 = 0, 1
+V_HARMONIC, V_LATTICE, V_STIRRER, V_ARRAY = 0, 1, 2, 3
+_DISC = {"fourier": FOURIER, "sine": SINE, "fd": FD}
+
+STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_ECUDA", 3: "GPE_ENOMEM",
+          4: "GPE_ENONFINITE", 5: "GPE_ENOCONV", 6: "GPE_ETIMEOUT"}
+
+
+class GPEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("disc", C.c_int), ("beta", C.c_double), ("omega", C.c_double), ("is_complex", C.c_int),
+                ("v_kind", C.c_int), ("v_param", C.c_double * 8), ("v_host", C.POINTER(C.c_double))]
+
+    @classmethod
+    def from_params(cls, p):
+        """From a workload parameter dict (see workloads.problem)."""
+        pr = cls()
+        pr.dim = p["dim"]
+        for a in range(3):
+            pr.n[a] = p["n"][a] if a < p["dim"] else 1
+            pr.lo[a] = p["lo"][a] if a < p["dim"] else 0.0
+            pr.hi[a] = p["hi"][a] if a < p["dim"] else 1.0
+        pr.disc = _DISC[p["disc"]]
+        pr.beta = p["beta"]
+        pr.omega = p["omega"]
+        pr.is_complex = 1 if p["is_complex"] else 0
+        pot = p["potential"]
+        g = pot.get("gamma", (1.0, 1.0, 1.0))
+        for a in range(3):
+            pr.v_param[a] = g[a] if a < len(g) else 1.0
+        kind = pot["kind"]
+        if kind == "harmonic":
+            pr.v_kind = V_HARMONIC
+        elif kind == "lattice":
+            pr.v_kind = V_LATTICE
+            pr.v_param[3] = pot["depth"]
+            pr.v_param[4] = pot["k"]
+        elif kind == "stirrer":
+            pr.v_kind = V_STIRRER
+            pr.v_param[3] = pot["w0"]
+            pr.v_param[4] = pot["delta"]
+            pr.v_param[5] = pot["r0"]
+        else:
+            raise ValueError(kind)
+        return pr
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("levels", C.c_int), ("mode", C.c_int), ("method", C.c_int), ("k_init", C.c_int),
+                ("k_sub", C.c_int), ("max_outer", C.c_int), ("max_iter", C.c_int), ("eps0", C.c_double),
+                ("delta_stop", C.c_double), ("res_tol", C.c_double), ("delta0", C.c_double),
+                ("switch_rel", C.c_double), ("chunk", C.c_int), ("use_graphs", C.c_int)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("E", C.c_double), ("mu", C.c_double), ("res", C.c_double), ("status", C.c_int),
+                ("outer_f32", C.c_int), ("outer_f64", C.c_int), ("inner_f32", C.c_int), ("inner_f64", C.c_int),
+                ("nfe", C.c_int), ("ms_f32", C.c_double), ("ms_f64", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load libgpe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgpe.so not built at {LIB_PATH}; run "
+                          "`python -m paper_1504_02891_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "gpe_plan_create": ([C.POINTER(Problem), ip, ip, vp, C.POINTER(vp)], ip),
+        "gpe_plan_destroy": ([vp], ip),
+        "gpe_last_error": ([], C.c_char_p),
+        "gpe_plan_size": ([vp, C.POINTER(C.c_int64), dp], ip),
+        "gpe_energy": ([vp, vp, dp, dp, dp], ip),
+        "gpe_grad": ([vp, vp, vp, dp, dp], ip),
+        "gpe_hessvec": ([vp, vp, vp, C.c_double, vp], ip),
+        "gpe_feasible_step": ([vp, vp, vp, C.c_double, vp, dp], ip),
+        "gpe_prolong": ([vp, vp, vp, vp], ip),
+        "gpe_solve_opts_default": ([C.POINTER(SolveOpts)], ip),
+        "gpe_rnewton_solve": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveReport)], ip),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+lib = None
+try:
+    lib = load()
+except ImportError:
+    # The module stays importable for build(); every call below raises.
+    lib = None
+
+
+def _check(st, allow=()):
+    if st != 0 and st not in allow:
+        raise GPEError(st, load().gpe_last_error().decode())
+    return st
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dbuf(n):
+    return (C.c_double * n)()
+
+
+class Plan:
+    """Owns a gpe_plan.  ``params`` is a workload parameter dict."""
+
+    def __init__(self, params, nbatch=1, prec=F64, stream=None):
+        import torch
+        L = load()
+        self.params = params
+        self.nbatch = nbatch
+        self.prec = prec
+        self.problem = Problem.from_params(params)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(L.gpe_plan_create(C.byref(self.problem), nbatch, prec, C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.handle = h
+        n = C.c_int64()
+        hv = C.c_double()
+        _check(L.gpe_plan_size(h, C.byref(n), C.byref(hv)))
+        self.M = n.value
+        self.h_vol = hv.value
+        ext = []
+        for a in range(params["dim"]):
+            N = params["n"][a]
+            ext.append(N if params["disc"] == "fourier" else N - 1)
+        self.shape = tuple(reversed(ext))
+        self.is_complex = bool(params["is_complex"])
+
+    @property
+    def dtype(self):
+        import torch
+        if self.is_complex:
+            return torch.complex64 if self.prec == F32 else torch.complex128
+        return torch.float32 if self.prec == F32 else torch.float64
+
+    def empty(self):
+        import torch
+        shape = (self.nbatch,) + self.shape if self.nbatch > 1 else self.shape
+        return torch.empty(shape, dtype=self.dtype, device="cuda")
+
+    def _chk(self, t):
+        if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != self.M * self.nbatch:
+            raise ValueError(f"expected contiguous CUDA {self.dtype} tensor with {self.M * self.nbatch} elements")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().gpe_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points --------------------------------------------------------
+    def energy(self, psi):
+        self._chk(psi)
+        E, mu, n2 = _dbuf(self.nbatch), _dbuf(self.nbatch), _dbuf(self.nbatch)
+        _check(load().gpe_energy(self.handle, _ptr(psi), E, mu, n2))
+        if self.nbatch == 1:
+            return E[0], mu[0], n2[0]
+        return list(E), list(mu), list(n2)
+
+    def grad(self, psi, out=None, with_energy=False):
+        self._chk(psi)
+        out = self.empty() if out is None else out
+        self._chk(out)
+        if with_energy:
+            E, mu = _dbuf(self.nbatch), _dbuf(self.nbatch)
+            _check(load().gpe_grad(self.handle, _ptr(psi), _ptr(out), E, mu))
+            return out, (E[0], mu[0]) if self.nbatch == 1 else (list(E), list(mu))
+        _check(load().gpe_grad(self.handle, _ptr(psi), _ptr(out), None, None))
+        return out
+
+    def hessvec(self, psi, d, shift=0.0, out=None):
+        self._chk(psi)
+        self._chk(d)
+        out = self.empty() if out is None else out
+        self._chk(out)
+        _check(load().gpe_hessvec(self.handle, _ptr(psi), _ptr(d), float(shift), _ptr(out)))
+        return out
+
+    def feasible_step(self, psi, hpsi, tau, out=None, with_energy=False):
+        self._chk(psi)
+        self._chk(hpsi)
+        out = self.empty() if out is None else out
+        self._chk(out)
+        if with_energy:
+            E = _dbuf(self.nbatch)
+            _check(load().gpe_feasible_step(self.handle, _ptr(psi), _ptr(hpsi), float(tau), _ptr(out), E))
+            return out, (E[0] if self.nbatch == 1 else list(E))
+        _check(load().gpe_feasible_step(self.handle, _ptr(psi), _ptr(hpsi), float(tau), _ptr(out), None))
+        return out
+
+    def prolong_to(self, fine, psi_c, out=None):
+        self._chk(psi_c)
+        out = fine.empty() if out is None else out
+        fine._chk(out)
+        _check(load().gpe_prolong(self.handle, fine.handle, _ptr(psi_c), _ptr(out)))
+        return out
+
+    def solve(self, psi, **opts):
+        """gpe_rnewton_solve in place on psi; returns the report as a dict."""
+        self._chk(psi)
+        o = SolveOpts()
+        _check(load().gpe_solve_opts_default(C.byref(o)))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        r = SolveReport()
+        _check(load().gpe_rnewton_solve(self.handle, _ptr(psi), C.byref(o), C.byref(r)), allow=(5,))
+        return r.as_dict()
+
+
+def default_opts():
+    o = SolveOpts()
+    _check(load().gpe_solve_opts_default(C.byref(o)))
+    return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def to_device(arr, prec=F64):
+    """numpy grid function -> contiguous CUDA tensor of the plan dtype."""
+    import torch
+    a = np.ascontiguousarray(arr)
+    if np.iscomplexobj(a):
+        t = torch.from_numpy(a.astype(np.complex64 if prec == F32 else np.complex128))
+    else:
+        t = torch.from_numpy(a.astype(np.float32 if prec == F32 else np.float64))
+    return t.cuda()
+
+
+def unit_scale(h_vol):
+    return math.sqrt(h_vol)

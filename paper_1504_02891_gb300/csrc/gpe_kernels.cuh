@@ -1,0 +1,133 @@
+// gpe_kernels.cuh -- device code of libgpe (sm_103a).
+//
+// The discretised GP operator of the paper (§2) is applied matrix-free as a sum
+// of per-axis line operators: along every axis, each grid line is transformed
+// (Fourier: an N-point DFT, Eq. fftp36; sine: the DST-I of Eq. tpll computed as
+// the 2N-point DFT of the odd extension), multiplied by the line's symbol
+// (lam^2/2, plus the folded rotation term +Omega*y*lam on x-lines and
+// -Omega*x*eta on y-lines, Eq. energy-discrete-FP), and transformed back
+// (Eq. fftp35 / spdo1).  One CTA owns a tile of lines in shared memory for the
+// whole forward-multiply-inverse sequence, so a pass reads its input once and
+// writes its output once.  The last pass of an application fuses the pointwise
+// terms (V, the cubic term, Lemma 3.1's Hessian terms) and float64 block
+// reductions; the last CTA to finish folds the per-CTA partials in a fixed
+// order (deterministic) and, in the solver, runs Algorithm 1's step-size logic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpe {
+
+template <typename T> struct C2t;
+template <> struct C2t<float> { using type = float2; };
+template <> struct C2t<double> { using type = double2; };
+
+constexpr int NTHREADS = 256;
+constexpr int NQ = 14;         // reduction slots per launch and instance
+
+// Reduction slots of the solver's evaluation passes (EPI_F / EPI_W).
+enum {
+  Q_E2 = 0,    // Re sum conj(y) (H_lin y)          -> 1/2 Y^*AY
+  Q_E4 = 1,    // sum |y|^4
+  Q_NY = 2,    // sum |y|^2
+  Q_YG = 3,    // Re sum conj(y) g
+  Q_GG = 4,    // sum |g|^2
+  Q_Q = 5,     // sum |g - th_c y|^2
+  Q_QY = 6,    // Re sum conj(g - th_c y) y
+  Q_SS = 7,    // sum |s|^2,     s = y - x_c
+  Q_SV = 8,    // Re sum conj(s) v,  v = g - g_c - th_c s
+  Q_VV = 9,    // sum |v|^2
+  Q_VY = 10,   // Re sum conj(v) y
+  Q_SY = 11,   // Re sum conj(s) y
+  Q_WX = 12,   // W objective: non-quadratic part of W^(k)
+  Q_MAX = 13   // max |s_j| (max-reduction)
+};
+// Slots of the ratio pass (EPI_RATIO), d = Z - X^k.
+enum { R_AXD = 0, R_DAD = 1, R_QD = 2, R_X2D2 = 3, R_R2 = 4, R_DD = 5, R_GD = 6 };
+
+enum Epi { EPI_ACC = 0, EPI_GRAD = 1, EPI_HESS = 2, EPI_F = 3, EPI_W = 4, EPI_RATIO = 5 };
+
+// Device-resident state of one Algorithm 1 run (one instance).  The passes read
+// the slot indices and scalars at their start; the last CTA of the final pass
+// updates them (see alg1_control).
+struct Alg1Ctl {
+  // configuration (host-written before the run)
+  double alpha;        // beta / (2 h_vol)
+  double delta;        // W objective: regularisation delta^(k)
+  double rho1, eta, delta_bt, eps0, res_tol, res_rel, tau0, renorm_tol;
+  int max_bt, max_iter, objective, always_renorm;
+  // slot state
+  int cur, prev, trial, has_cur, done, status, phase, pad0;
+  double theta_c;      // theta of the current point (used by the passes)
+  // iteration state
+  int k, m, nfe, accepted_last;
+  double tau, C, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;
+  double a, b, s;      // Cayley step coefficients of the next trial
+  double res;          // ||A(X)X||_2 of the current point
+};
+
+// Outer state of Algorithm 2 (ratio test), written by the ratio pass.
+struct RNCtl {
+  double alpha, delta, eta1, eta2, gamma1, gamma2, delta_min, delta_max, F_k;
+  double ared, pred, rho, dmax;
+  int accepted, pad;
+};
+
+template <typename T>
+struct PassGeom {
+  int axis;             // 0 (x), 1 (y), 2 (z)
+  int n0, n1, n2;       // extents of one instance
+  long long M;          // unknowns per instance
+  int len;              // extent along the axis
+  long long stride;     // element stride along the axis
+  long long ostride;    // axes 1,2: stride of the outer index
+  int F, logF;          // FFT length
+  int odd_ext;          // sine grid: odd extension to 2N
+  int LB;               // data lines per tile
+  int LC;               // complex lines per tile
+  int tiles;            // tiles per instance
+  int xt;               // axes 1,2: tiles along x
+  const typename C2t<T>::type* tw;  // e^{-2 pi i k / F}
+  const T* lam;         // wavenumber of FFT index m
+  T c2, c1;             // symbol = c2*lam^2 + c1*coord*lam  (1/F folded in)
+  const T* rcoord;      // rotation coordinate table (x or y nodes) or null
+};
+
+struct FDGeom {
+  int dim, n0, n1, n2;
+  long long M;
+  double ih2[3];        // 1/h_a^2
+  double ih2c[3];       // 1/(2 h_a) for the central differences
+  double omega;
+  int tiles;            // blocks per instance
+};
+
+template <typename T>
+struct PassData {
+  const void* x;        // input vector (ABI modes); solver: resolved from slots
+  const void* xsub;     // optional: input = x - xsub
+  const void* acc_in;   // kinetic part of earlier passes (or null)
+  void* out;            // EPI_ACC: accumulator; final: output vector (or null)
+  // solver slots
+  void* const* xs;      // 3 X slots
+  void* const* gs;      // 3 G slots
+  Alg1Ctl* ctl;         // non-null in solver mode
+  RNCtl* rn;            // ratio pass
+  int step_on_load;     // Y = s(a X_cur + b G_cur) formed on load, stored to xs[trial]
+  int use_slots;        // x = xs[trial], out = gs[trial] (final), xc/gc from slots
+  // pointwise data
+  const T* V;
+  const void* base;     // HESS: psi; W, RATIO: X^k
+  const void* gk;       // RATIO: G_k
+  double nl;            // ABI: beta; solver: alpha (read from ctl when null)
+  double shift;         // HESS shift
+  double lin_scale;     // 1 (ABI) or 2 (unified A = 2 H_lin)
+  // reductions
+  double* partials;     // [gridDim.x][NQ]
+  double* results;      // [nbatch][NQ]
+  unsigned int* ticket;
+  int nq;               // active slots (0: none)
+  int control;          // 0: none, 1: Algorithm 1 control, 2: ratio control
+};
+
+}  // namespace gpe

@@ -1,0 +1,30 @@
+// Float64 instantiation of the libgpe kernels and launch wrappers.
+#include "ops_launch.cuh"
+namespace gpe {
+GPE_INSTANTIATE(double)
+}  // namespace gpe
+
+namespace gpe {
+template <typename Ti, typename To>
+gpe_status launch_convert(const Ti* in, To* out, long long n, double scale, cudaStream_t st) {
+  k_convert<Ti, To><<<ew_blocks(n), NTHREADS, 0, st>>>(in, out, n, scale);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
+}
+template gpe_status launch_convert<float, double>(const float*, double*, long long, double, cudaStream_t);
+template gpe_status launch_convert<double, float>(const double*, float*, long long, double, cudaStream_t);
+template gpe_status launch_convert<float, float>(const float*, float*, long long, double, cudaStream_t);
+template gpe_status launch_convert<double, double>(const double*, double*, long long, double, cudaStream_t);
+
+gpe_status launch_step_coef(const double* mom, int nbatch, double h, double tau, double* coef, cudaStream_t st) {
+  k_step_coef<<<(nbatch + 127) / 128, 128, 0, st>>>(mom, nbatch, h, tau, coef);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
+}
+
+gpe_status launch_norm_coef(const double* mom, int nbatch, double h, double* coef, cudaStream_t st) {
+  k_norm_coef<<<(nbatch + 127) / 128, 128, 0, st>>>(mom, nbatch, h, coef);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
+}
+}  // namespace gpe

@@ -1,0 +1,576 @@
+// solver.cu -- gpe_rnewton_solve: Algorithm 3 (cascade) around Algorithm 2
+// (regularized Newton with the trust-region ratio test) and Algorithm 1
+// (feasible gradient with BB steps and the nonmonotone curvilinear search).
+//
+// Every numerical step runs on the device: an Algorithm 1 iteration is the
+// operator passes with the Cayley step formed while loading the first pass and
+// the step-size logic executed by the last CTA of the final pass (alg1_control).
+// The host only queues fixed chunks of iterations (captured once in a CUDA
+// graph per level and objective) and reads the small control block between
+// chunks to learn whether the run has stopped.
+#include <math.h>
+#include <string.h>
+#include <chrono>
+#include <memory>
+#include <vector>
+#include "gpe_internal.h"
+
+namespace gpe {
+
+template <typename T>
+struct Level {
+  GridHost g;
+  GridDev<T> d;
+  Scratch sc;
+  long long M = 0;
+  size_t bytes = 0;
+  void* acc = nullptr;
+  void* xs[3] = {nullptr, nullptr, nullptr};
+  void* gs[3] = {nullptr, nullptr, nullptr};
+  void* xk = nullptr;
+  void* gk = nullptr;
+  void** d_xs = nullptr;
+  void** d_gs = nullptr;
+  Alg1Ctl* ctl = nullptr;
+  RNCtl* rn = nullptr;
+  Alg1Ctl* h_ctl = nullptr;
+  RNCtl* h_rn = nullptr;
+  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};   // objective F, W
+  int chunk_len = 0;
+
+  gpe_status create(const GridHost& gh) {
+    g = gh;
+    M = g.M;
+    bytes = sizeof(T) * (g.is_complex ? 2 : 1) * M;
+    gpe_status s = d.create(g);
+    if (s != GPE_OK) return s;
+    s = sc.create(d.max_blocks, 1);
+    if (s != GPE_OK) return s;
+    GPE_CUDA(cudaMalloc(&acc, bytes));
+    for (int i = 0; i < 3; ++i) {
+      GPE_CUDA(cudaMalloc(&xs[i], bytes));
+      GPE_CUDA(cudaMalloc(&gs[i], bytes));
+    }
+    GPE_CUDA(cudaMalloc(&xk, bytes));
+    GPE_CUDA(cudaMalloc(&gk, bytes));
+    GPE_CUDA(cudaMalloc(&d_xs, sizeof(void*) * 3));
+    GPE_CUDA(cudaMalloc(&d_gs, sizeof(void*) * 3));
+    GPE_CUDA(cudaMemcpy(d_xs, xs, sizeof(void*) * 3, cudaMemcpyHostToDevice));
+    GPE_CUDA(cudaMemcpy(d_gs, gs, sizeof(void*) * 3, cudaMemcpyHostToDevice));
+    GPE_CUDA(cudaMalloc(&ctl, sizeof(Alg1Ctl)));
+    GPE_CUDA(cudaMalloc(&rn, sizeof(RNCtl)));
+    GPE_CUDA(cudaMallocHost(&h_ctl, sizeof(Alg1Ctl)));
+    GPE_CUDA(cudaMallocHost(&h_rn, sizeof(RNCtl)));
+    memset(h_ctl, 0, sizeof(Alg1Ctl));
+    memset(h_rn, 0, sizeof(RNCtl));
+    return GPE_OK;
+  }
+  void destroy() {
+    for (int i = 0; i < 2; ++i)
+      if (chunk_exec[i]) cudaGraphExecDestroy(chunk_exec[i]);
+    d.destroy();
+    sc.destroy();
+    cudaFree(acc);
+    for (int i = 0; i < 3; ++i) {
+      cudaFree(xs[i]);
+      cudaFree(gs[i]);
+    }
+    cudaFree(xk);
+    cudaFree(gk);
+    cudaFree(d_xs);
+    cudaFree(d_gs);
+    cudaFree(ctl);
+    cudaFree(rn);
+    cudaFreeHost(h_ctl);
+    cudaFreeHost(h_rn);
+  }
+  PassData<T> solver_data(int objective) const {
+    PassData<T> D{};
+    D.xs = d_xs;
+    D.gs = d_gs;
+    D.ctl = ctl;
+    D.use_slots = 1;
+    D.V = d.V;
+    D.lin_scale = 2.0;
+    D.base = objective == 1 ? xk : nullptr;
+    D.partials = sc.partials;
+    D.results = sc.results;
+    D.ticket = sc.ticket;
+    D.nq = NQ;
+    D.control = 1;
+    return D;
+  }
+};
+
+struct RunStats {
+  int iters = 0, nfe = 0, status = 0;
+  double F = 0, res = 0, theta = 0;
+};
+
+struct SolveParams {
+  int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs;
+  double eps0, delta_stop, res_tol_X, delta0, switch_rel;
+};
+
+template <typename T>
+static gpe_status read_ctl(Level<T>& L, cudaStream_t st) {
+  GPE_CUDA(cudaMemcpyAsync(L.h_ctl, L.ctl, sizeof(Alg1Ctl), cudaMemcpyDeviceToHost, st));
+  GPE_CUDA(cudaStreamSynchronize(st));
+  return GPE_OK;
+}
+
+// Queue `n` Algorithm 1 iterations (each: Cayley step formed on load, the
+// operator passes, control in the last CTA).
+template <typename T>
+static gpe_status queue_iters(Level<T>& L, int objective, int n, cudaStream_t st) {
+  const PassData<T> D = L.solver_data(objective);
+  const int epi = objective == 1 ? EPI_W : EPI_F;
+  for (int i = 0; i < n; ++i) {
+    gpe_status s = apply_op<T>(L.g, L.d, D, epi, L.acc, true, st);
+    if (s != GPE_OK) return s;
+  }
+  return GPE_OK;
+}
+
+template <typename T>
+static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cudaStream_t st) {
+  if (!P.use_graphs) return queue_iters<T>(L, objective, P.chunk, st);
+  cudaGraphExec_t& ex = L.chunk_exec[objective];
+  if (!ex || L.chunk_len != P.chunk) {
+    if (ex) {
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+    cudaGraph_t graph;
+    GPE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    gpe_status s = queue_iters<T>(L, objective, P.chunk, st);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != GPE_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    L.chunk_len = P.chunk;
+  }
+  GPE_CUDA(cudaGraphLaunch(ex, st));
+  return GPE_OK;
+}
+
+// Algorithm 1 on objective F (0) or W^(k) (1) from the point in xs[first_slot]
+// (unit norm).  Returns the state of the control block in L.h_ctl.
+template <typename T>
+static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_iter, double res_tol, double eps0,
+                           double delta, const SolveParams& P, cudaStream_t st, RunStats& out, double res_rel = 0.0) {
+  Alg1Ctl& c = *L.h_ctl;
+  memset(&c, 0, sizeof(c));
+  c.alpha = L.g.beta / (2.0 * L.g.hvol);
+  c.delta = delta;
+  c.rho1 = 1e-4;
+  c.eta = 0.85;
+  c.delta_bt = 0.1;
+  c.eps0 = eps0;
+  c.res_tol = res_tol;
+  c.res_rel = res_rel;
+  c.tau0 = 1e-3;
+  c.renorm_tol = 1e-14;
+  c.max_bt = 10;
+  c.max_iter = max_iter;
+  c.objective = objective;
+  c.always_renorm = sizeof(T) == 4 ? 1 : 0;
+  c.cur = 0;
+  c.prev = 1;
+  c.trial = first_slot;
+  c.has_cur = 0;
+  c.done = 0;
+  c.phase = 0;
+  GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
+  // first evaluation (no step)
+  gpe_status s = apply_op<T>(L.g, L.d, L.solver_data(objective), objective == 1 ? EPI_W : EPI_F, L.acc, false, st);
+  if (s != GPE_OK) return s;
+  // bounded: every queued iteration either accepts or backtracks (<= max_bt times)
+  const long long max_launch = (long long)(max_iter + 1) * (c.max_bt + 1) + 1;
+  long long launched = 0;
+  s = read_ctl<T>(L, st);
+  if (s != GPE_OK) return s;
+  while (!L.h_ctl->done && launched < max_launch) {
+    s = run_chunk<T>(L, objective, P, st);
+    if (s != GPE_OK) return s;
+    launched += P.chunk;
+    s = read_ctl<T>(L, st);
+    if (s != GPE_OK) return s;
+  }
+  out.iters = L.h_ctl->k;
+  out.nfe = L.h_ctl->nfe;
+  out.status = L.h_ctl->status;
+  out.F = L.h_ctl->F_cur;
+  out.res = L.h_ctl->res;
+  out.theta = L.h_ctl->theta_c;
+  if (L.h_ctl->status == GPE_ENONFINITE) return fail(GPE_ENONFINITE, "non-finite energy during Algorithm 1");
+  return GPE_OK;
+}
+
+struct LevelStats {
+  int outer = 0, inner = 0, nfe = 0;
+  double F = 0, res = 0, theta = 0;
+  bool converged = false;
+};
+
+// Algorithm 2 on one level, starting from xs[0]; result in xk/gk.
+// mode_f32: stop on the float32 criteria (relative residual or stagnation).
+template <typename T>
+static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool stop_f32, cudaStream_t st,
+                         LevelStats& ls) {
+  RunStats r;
+  const double res_tol = P.res_tol_X;
+  // warm start (Algorithm 1, <= k_init iterations; k_init = 0 is one evaluation)
+  gpe_status s = alg1_run<T>(L, 0, 0, k_init, res_tol, P.eps0, 0.0, P, st, r);
+  if (s != GPE_OK) return s;
+  ls.inner += r.iters;
+  ls.nfe += r.nfe;
+  double Fk = r.F, resk = r.res, thk = r.theta;
+  const int cur = L.h_ctl->cur;
+  GPE_CUDA(cudaMemcpyAsync(L.xk, L.xs[cur], L.bytes, cudaMemcpyDeviceToDevice, st));
+  GPE_CUDA(cudaMemcpyAsync(L.gk, L.gs[cur], L.bytes, cudaMemcpyDeviceToDevice, st));
+  double delta = P.delta0;
+  double best_res = resk;
+  int stall = 0, rejects = 0;
+  for (int outer = 0; outer < P.max_outer; ++outer) {
+    if (res_tol > 0.0 && resk <= res_tol) { ls.converged = true; break; }
+    if (stop_f32 && resk <= P.switch_rel * fabs(thk)) break;
+    // subproblem (Eq. tr-sub) by Algorithm 1 on W^(k) from X^k
+    GPE_CUDA(cudaMemcpyAsync(L.xs[0], L.xk, L.bytes, cudaMemcpyDeviceToDevice, st));
+    const double sub_tol = fmax(1e-2 * resk, 1e-14);
+    s = alg1_run<T>(L, 1, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r);
+    if (s != GPE_OK) return s;
+    ls.inner += r.iters;
+    ls.nfe += r.nfe;
+    const int zc = L.h_ctl->cur;
+    // ratio test (Eq. TR-ratio) and delta update (Eq. tau-up)
+    RNCtl& rc = *L.h_rn;
+    memset(&rc, 0, sizeof(rc));
+    rc.alpha = L.g.beta / (2.0 * L.g.hvol);
+    rc.delta = delta;
+    rc.eta1 = 0.01;
+    rc.eta2 = 0.9;
+    rc.gamma1 = 2.0;
+    rc.gamma2 = 4.0;
+    rc.delta_min = 1e-12;
+    rc.delta_max = 1e12;
+    rc.F_k = Fk;
+    GPE_CUDA(cudaMemcpyAsync(L.rn, &rc, sizeof(RNCtl), cudaMemcpyHostToDevice, st));
+    PassData<T> D{};
+    D.x = L.xs[zc];
+    D.xsub = L.xk;
+    D.base = L.xk;
+    D.gk = L.gk;
+    D.rn = L.rn;
+    D.V = L.d.V;
+    D.lin_scale = 2.0;
+    D.partials = L.sc.partials;
+    D.results = L.sc.results;
+    D.ticket = L.sc.ticket;
+    D.nq = NQ;
+    D.control = 2;
+    s = apply_op<T>(L.g, L.d, D, EPI_RATIO, L.acc, false, st);
+    if (s != GPE_OK) return s;
+    GPE_CUDA(cudaMemcpyAsync(L.h_rn, L.rn, sizeof(RNCtl), cudaMemcpyDeviceToHost, st));
+    GPE_CUDA(cudaStreamSynchronize(st));
+    ls.nfe += 1;
+    ls.outer += 1;
+    const bool accepted = L.h_rn->accepted != 0;
+    const double dmax = L.h_rn->dmax;
+    delta = L.h_rn->delta;
+    if (!isfinite(L.h_rn->rho)) return fail(GPE_ENONFINITE, "non-finite ratio in the regularized Newton step");
+    if (accepted) {
+      rejects = 0;
+      // gradient at the accepted point (Eq. update-X): one evaluation
+      s = alg1_run<T>(L, 0, zc, 0, 0.0, 0.0, 0.0, P, st, r);
+      if (s != GPE_OK) return s;
+      ls.nfe += r.nfe;
+      const int c2 = L.h_ctl->cur;
+      GPE_CUDA(cudaMemcpyAsync(L.xk, L.xs[c2], L.bytes, cudaMemcpyDeviceToDevice, st));
+      GPE_CUDA(cudaMemcpyAsync(L.gk, L.gs[c2], L.bytes, cudaMemcpyDeviceToDevice, st));
+      Fk = r.F;
+      resk = r.res;
+      thk = r.theta;
+      if (!stop_f32 && dmax <= P.delta_stop) { ls.converged = true; break; }   // Eq. crit2
+    } else {
+      ++rejects;
+    }
+    if (stop_f32) {
+      if (resk < 0.5 * best_res) {
+        best_res = resk;
+        stall = 0;
+      } else if (++stall >= 3) {
+        break;   // float32 stagnation
+      }
+      if (rejects >= 3) break;
+    }
+  }
+  ls.F = Fk;
+  ls.res = resk;
+  ls.theta = thk;
+  return GPE_OK;
+}
+
+// Algorithm 1 only (method = 1): result in xk/gk.
+template <typename T>
+static gpe_status fg_run(Level<T>& L, const SolveParams& P, bool stop_f32, cudaStream_t st, LevelStats& ls) {
+  RunStats r;
+  // float32: stop on the relative residual instead of Eq. crit1 (the step
+  // size test cannot see below float32 rounding)
+  const double eps0 = stop_f32 ? 0.0 : P.eps0;
+  gpe_status s = alg1_run<T>(L, 0, 0, P.max_iter, P.res_tol_X, eps0, 0.0, P, st, r, stop_f32 ? P.switch_rel : 0.0);
+  if (s != GPE_OK) return s;
+  const int cur = L.h_ctl->cur;
+  GPE_CUDA(cudaMemcpyAsync(L.xk, L.xs[cur], L.bytes, cudaMemcpyDeviceToDevice, st));
+  GPE_CUDA(cudaMemcpyAsync(L.gk, L.gs[cur], L.bytes, cudaMemcpyDeviceToDevice, st));
+  ls.inner += r.iters;
+  ls.nfe += r.nfe;
+  ls.F = r.F;
+  ls.res = r.res;
+  ls.theta = r.theta;
+  ls.converged = (r.status == 0);
+  return GPE_OK;
+}
+
+// X in xs[0] scaled to unit 2-norm.
+template <typename T>
+static gpe_status normalise_slot0(Level<T>& L, cudaStream_t st) {
+  gpe_status s = launch_moments<T>(L.xs[0], nullptr, L.M, 1, L.g.is_complex, L.sc, st);
+  if (s != GPE_OK) return s;
+  s = launch_norm_coef(L.sc.results, 1, 1.0, L.sc.coef, st);
+  if (s != GPE_OK) return s;
+  return launch_axpby<T>(L.xs[0], nullptr, L.sc.coef, 1, L.M, 1, L.xs[0], L.g.is_complex, st);
+}
+
+template <typename Ti, typename To>
+static gpe_status convert_vec(const void* in, void* out, long long n_real, double scale, cudaStream_t st) {
+  return launch_convert<Ti, To>((const Ti*)in, (To*)out, n_real, scale, st);
+}
+
+// Cache of solver levels kept in the plan between calls.
+struct SolverCache {
+  int levels = 0, mode = -1;
+  std::vector<std::unique_ptr<Level<float>>> lf;
+  std::vector<std::unique_ptr<Level<double>>> ld;
+  std::unique_ptr<Level<double>> fine64;   // float64 refinement/report level (modes 1, 2)
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  void* inj = nullptr;                     // injected initial guess (plan precision, coarse grid)
+  ~SolverCache() {
+    for (auto& l : lf) l->destroy();
+    for (auto& l : ld) l->destroy();
+    if (fine64) fine64->destroy();
+    if (st) cudaStreamDestroy(st);
+    if (ev) cudaEventDestroy(ev);
+    cudaFree(inj);
+  }
+};
+
+void destroy_solver_cache(void* p) { delete static_cast<SolverCache*>(p); }
+
+template <typename T>
+static gpe_status make_levels(const GridHost& fine, int levels, std::vector<std::unique_ptr<Level<T>>>& out) {
+  out.clear();
+  for (int l = 0; l < levels; ++l) {
+    GridHost g = grid_coarsen(fine, levels - 1 - l);
+    g.nbatch = 1;
+    std::unique_ptr<Level<T>> L(new Level<T>());
+    gpe_status s = L->create(g);
+    if (s != GPE_OK) {
+      L->destroy();
+      return s;
+    }
+    out.push_back(std::move(L));
+  }
+  return GPE_OK;
+}
+
+// Initial guess (plan precision, finest grid) -> xs[0] of the coarsest level (X units, unit norm).
+template <typename Tp, typename T>
+static gpe_status load_initial(gpe_plan plan, SolverCache& C, Level<T>& L0, const void* psi, bool inject) {
+  const long long nreal = L0.M * (L0.g.is_complex ? 2 : 1);
+  const void* src = psi;
+  if (inject) {
+    gpe_status s = launch_inject<Tp>(plan->g, L0.g, psi, C.inj, C.st);
+    if (s != GPE_OK) return s;
+    src = C.inj;
+  }
+  gpe_status s = convert_vec<Tp, T>(src, L0.xs[0], nreal, sqrt(L0.g.hvol), C.st);
+  if (s != GPE_OK) return s;
+  return normalise_slot0<T>(L0, C.st);
+}
+
+template <typename T>
+static gpe_status prolong_into(Level<T>& Lc, Level<T>& Lf, cudaStream_t st) {
+  gpe_status s = launch_prolong<T>(Lc.g, Lf.g, Lc.d, Lf.d, Lc.xk, Lf.xs[0], Lf.acc, Lf.gs[0], st);
+  if (s != GPE_OK) return s;
+  return normalise_slot0<T>(Lf, st);
+}
+
+template <typename T>
+static gpe_status solve_levels(std::vector<std::unique_ptr<Level<T>>>& lv, const SolveParams& P, bool f32,
+                               cudaStream_t st, LevelStats& fine_stats, int& nfe_total) {
+  for (size_t l = 0; l < lv.size(); ++l) {
+    if (l > 0) {
+      gpe_status s = prolong_into<T>(*lv[l - 1], *lv[l], st);
+      if (s != GPE_OK) return s;
+    }
+    LevelStats ls;
+    gpe_status s = P.method == 1 ? fg_run<T>(*lv[l], P, f32, st, ls) : rn_run<T>(*lv[l], P, P.k_init, f32, st, ls);
+    if (s != GPE_OK) return s;
+    nfe_total += ls.nfe;
+    if (l + 1 == lv.size()) fine_stats = ls;
+  }
+  return GPE_OK;
+}
+
+template <typename Tp>
+static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, gpe_solve_report& rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  SolverCache*& C = reinterpret_cast<SolverCache*&>(plan->solver_cache);
+  if (C && (C->levels != o.levels || C->mode != o.mode)) {
+    cudaStreamSynchronize(C->st);
+    delete C;
+    C = nullptr;
+  }
+  if (!C) {
+    C = new SolverCache();
+    C->levels = o.levels;
+    C->mode = o.mode;
+    GPE_CUDA(cudaStreamCreateWithFlags(&C->st, cudaStreamNonBlocking));
+    GPE_CUDA(cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming));
+    gpe_status s = GPE_OK;
+    if (o.mode == 0) s = make_levels<double>(plan->g, o.levels, C->ld);
+    else s = make_levels<float>(plan->g, o.levels, C->lf);
+    if (s == GPE_OK && o.mode != 0) {
+      GridHost g = plan->g;
+      g.nbatch = 1;
+      C->fine64.reset(new Level<double>());
+      s = C->fine64->create(g);
+    }
+    if (s == GPE_OK) {
+      cudaError_t e = cudaMalloc(&C->inj, elem_size(plan->prec, plan->g.is_complex) * plan->g.M);
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc(injection)");
+    }
+    if (s != GPE_OK) {
+      delete C;
+      C = nullptr;
+      return s;
+    }
+  }
+  cudaStream_t st = C->st;
+  // order after the caller's stream
+  GPE_CUDA(cudaEventRecord(C->ev, plan->stream));
+  GPE_CUDA(cudaStreamWaitEvent(st, C->ev, 0));
+
+  SolveParams P;
+  P.k_init = o.k_init;
+  P.k_sub = o.k_sub;
+  P.max_outer = o.max_outer;
+  P.max_iter = o.max_iter;
+  P.method = o.method;
+  P.chunk = o.chunk;
+  P.use_graphs = o.use_graphs;
+  P.eps0 = o.eps0;
+  P.delta_stop = o.delta_stop;
+  P.res_tol_X = 2.0 * o.res_tol;     // ||A(X)X||_2 = 2 ||H psi - mu psi||_h
+  P.delta0 = o.delta0;
+  P.switch_rel = o.switch_rel;
+
+  const bool inject = o.levels > 1;
+  LevelStats fs;
+  int nfe = 0;
+  gpe_status s;
+  Level<double>* fin = nullptr;
+  if (o.mode == 0) {
+    s = load_initial<Tp, double>(plan, *C, *C->ld[0], psi, inject);
+    if (s != GPE_OK) return s;
+    s = solve_levels<double>(C->ld, P, false, st, fs, nfe);
+    if (s != GPE_OK) return s;
+    fin = C->ld.back().get();
+    rep.outer_f64 = fs.outer;
+    rep.inner_f64 = fs.inner;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    rep.ms_f64 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  } else {
+    s = load_initial<Tp, float>(plan, *C, *C->lf[0], psi, inject);
+    if (s != GPE_OK) return s;
+    s = solve_levels<float>(C->lf, P, true, st, fs, nfe);
+    if (s != GPE_OK) return s;
+    rep.outer_f32 = fs.outer;
+    rep.inner_f32 = fs.inner;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    auto t1 = std::chrono::steady_clock::now();
+    rep.ms_f32 = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    // float64 refinement (mode 1) or float64 evaluation of the result (mode 2)
+    Level<float>& Lf = *C->lf.back();
+    fin = C->fine64.get();
+    const long long nreal = Lf.M * (Lf.g.is_complex ? 2 : 1);
+    s = convert_vec<float, double>(Lf.xk, fin->xs[0], nreal, 1.0, st);
+    if (s != GPE_OK) return s;
+    s = normalise_slot0<double>(*fin, st);
+    if (s != GPE_OK) return s;
+    LevelStats ls;
+    if (o.mode == 1) {
+      SolveParams P64 = P;
+      s = rn_run<double>(*fin, P64, 0, false, st, ls);
+      rep.outer_f64 = ls.outer;
+      rep.inner_f64 = ls.inner;
+    } else {
+      SolveParams P64 = P;
+      P64.max_outer = 0;
+      s = rn_run<double>(*fin, P64, 0, false, st, ls);
+    }
+    if (s != GPE_OK) return s;
+    nfe += ls.nfe;
+    fs = ls;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    rep.ms_f64 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  }
+  // result: X (float64 or bulk precision) -> psi in plan precision
+  const long long nreal = fin->M * (fin->g.is_complex ? 2 : 1);
+  const double inv_s = 1.0 / sqrt(fin->g.hvol);
+  if (plan->prec == GPE_F64) s = convert_vec<double, double>(fin->xk, psi, nreal, inv_s, st);
+  else s = convert_vec<double, float>(fin->xk, psi, nreal, inv_s, st);
+  if (s != GPE_OK) return s;
+  GPE_CUDA(cudaEventRecord(C->ev, st));
+  GPE_CUDA(cudaStreamWaitEvent(plan->stream, C->ev, 0));
+  GPE_CUDA(cudaStreamSynchronize(st));
+  rep.E = fs.F;
+  rep.mu = 0.5 * fs.theta;
+  rep.res = 0.5 * fs.res;
+  rep.nfe = nfe;
+  rep.status = fs.converged ? GPE_OK : GPE_ENOCONV;
+  if (o.mode == 2) rep.status = GPE_OK;
+  return GPE_OK;
+}
+
+}  // namespace gpe
+
+using namespace gpe;
+
+extern "C" gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
+                                        gpe_solve_report* report) {
+  if (!plan || !psi_inout) return fail(GPE_EINVAL, "plan or psi is NULL");
+  if (plan->g.nbatch != 1) return fail(GPE_EINVAL, "gpe_rnewton_solve needs a plan with nbatch = 1");
+  gpe_solve_opts o;
+  if (opts) o = *opts;
+  else gpe_solve_opts_default(&o);
+  if (o.levels < 1 || o.mode < 0 || o.mode > 2 || o.method < 0 || o.method > 1 || o.chunk < 1 || o.k_init < 0 ||
+      o.k_sub < 1 || o.max_outer < 0 || o.max_iter < 0 || !(o.res_tol >= 0) || !(o.delta0 > 0))
+    return fail(GPE_EINVAL, "invalid solve options");
+  for (int a = 0; a < plan->g.dim; ++a) {
+    const int nc = plan->g.N[a] >> (o.levels - 1);
+    if ((nc << (o.levels - 1)) != plan->g.N[a] || nc < 4)
+      return fail(GPE_EINVAL, "too many cascade levels for this grid (coarsest n must be >= 4)");
+  }
+  gpe_solve_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gpe_status s = plan->prec == GPE_F64 ? solve_impl<double>(plan, psi_inout, o, rep)
+                                       : solve_impl<float>(plan, psi_inout, o, rep);
+  if (report) *report = rep;
+  if (s != GPE_OK) return s;
+  return rep.status == GPE_ENOCONV ? GPE_ENOCONV : GPE_OK;
+}

@@ -1,0 +1,62 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+and exports every entry point declared in include/gpe.h."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gpe_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("gpe_plan_create", "gpe_plan_destroy", "gpe_energy", "gpe_grad", "gpe_hessvec",
+              "gpe_feasible_step", "gpe_rnewton_solve", "gpe_prolong", "gpe_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1504_02891_gb300 import build as B
+    lib_path = B.build()
+    lib = ctypes.CDLL(lib_path)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    # error text is available without a device
+    lib.gpe_last_error.restype = ctypes.c_char_p
+    assert lib.gpe_last_error() is not None
+
+
+def test_invalid_problem_rejected_without_device():
+    """Shape validation happens on the host before any CUDA call."""
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1504_02891_gb300 import build as B
+    B.build()
+    import paper_1504_02891_gb300 as G
+    import workloads as W
+    L = G.load()
+    bad = [W.problem(2, (100, 64), (-1, -1), (1, 1), "fourier"),           # not a power of two
+           W.problem(2, (64, 64), (-1, -1), (1, 1), "sine", omega=0.5, is_complex=True),
+           W.problem(1, (64,), (-1,), (1,), "fourier", omega=0.5, is_complex=True)]
+    for p in bad:
+        pr = G.Problem.from_params(p)
+        h = ctypes.c_void_p()
+        st = L.gpe_plan_create(ctypes.byref(pr), 1, G.F64, None, ctypes.byref(h))
+        assert st == 1, (p, st)
+        assert len(L.gpe_last_error()) > 0

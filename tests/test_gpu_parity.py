@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every GPU result here is compared element by element with the oracle on the
+same seeded input bytes.  Tolerances: operator applications within 1e-12
+(float64) and 2e-5 (float32) relative to the largest reference value;
+energies/ground states as stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1504_02891_gb300 as G  # noqa: E402
+
+TOL = {G.F64: 1e-12, G.F32: 2e-5}
+
+
+def host(t):
+    a = t.detach().cpu().numpy()
+    return a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def as_prec(a, prec):
+    """The input exactly as the device sees it (rounded to the plan precision)."""
+    if prec == G.F32:
+        return a.astype(np.complex64 if np.iscomplexobj(a) else np.float32).astype(
+            np.complex128 if np.iscomplexobj(a) else np.float64)
+    return a
+
+
+def oracle_hpsi(g, psi):
+    return O.apply_hlin(g, psi) + g.beta * np.abs(psi) ** 2 * psi
+
+
+OPERATOR_CASES = [
+    # name, params
+    ("fp1d", W.problem(1, (64,), (-8.0,), (8.0,), "fourier", beta=37.0)),
+    ("fp1d_tiny", W.problem(1, (4,), (-2.0,), (2.0,), "fourier", beta=3.0)),
+    ("fp2d_real", W.problem(2, (32, 64), (-6.0, -7.0), (6.0, 9.0), "fourier", beta=50.0,
+                            potential={"kind": "harmonic", "gamma": (1.0, 1.3)})),
+    ("fp2d_rot", W.problem(2, (64, 32), (-8.0, -6.0), (8.0, 6.0), "fourier", beta=80.0, omega=0.7,
+                           is_complex=True)),
+    ("fp2d_rot_big", W.problem(2, (256, 128), (-16.0, -12.0), (16.0, 12.0), "fourier", beta=1000.0,
+                               omega=0.9, is_complex=True)),
+    ("fp3d_real", W.problem(3, (16, 32, 8), (-5.0,) * 3, (5.0,) * 3, "fourier", beta=20.0)),
+    ("fp3d_rot", W.problem(3, (16, 8, 16), (-5.0,) * 3, (5.0,) * 3, "fourier", beta=20.0, omega=0.4,
+                           is_complex=True)),
+    ("sp1d", W.problem(1, (64,), (-8.0,), (8.0,), "sine", beta=25.0,
+                       potential={"kind": "lattice", "gamma": (1.0,), "depth": 25.0, "k": math.pi / 4})),
+    ("sp1d_tiny", W.problem(1, (4,), (-2.0,), (2.0,), "sine", beta=1.0)),
+    ("sp2d", W.problem(2, (32, 16), (-8.0, -4.0), (8.0, 4.0), "sine", beta=100.0)),
+    ("sp2d_ragged", W.problem(2, (128, 128), (-16.0, -16.0), (16.0, 16.0), "sine", beta=500.0,
+                              potential={"kind": "lattice", "gamma": (1.0, 1.0), "depth": 50.0, "k": math.pi / 4})),
+    ("sp3d", W.problem(3, (16, 8, 32), (-8.0,) * 3, (8.0,) * 3, "sine", beta=800.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0, 1.0), "depth": 50.0, "k": math.pi / 4})),
+    ("fd1d", W.problem(1, (50,), (-8.0,), (8.0,), "fd", beta=30.0)),
+    ("fd2d_rot", W.problem(2, (20, 33), (-6.0, -6.0), (6.0, 7.0), "fd", beta=10.0, omega=0.6, is_complex=True)),
+    ("fd3d", W.problem(3, (10, 12, 9), (-4.0,) * 3, (4.0,) * 3, "fd", beta=5.0,
+                       potential={"kind": "stirrer", "gamma": (1.0, 1.0, 2.0), "w0": 4.0, "delta": 1.0, "r0": 1.0})),
+]
+
+
+@pytest.mark.parametrize("prec", [G.F64, G.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("name,p", OPERATOR_CASES, ids=[c[0] for c in OPERATOR_CASES])
+def test_grad_energy_hessvec_parity(name, p, prec):
+    g = O.build_grid(p)
+    psi = as_prec(W.random_field(p, seed=11, smooth=0.02), prec)
+    d = as_prec(W.random_field(p, seed=12), prec)
+    with G.Plan(p, prec=prec) as plan:
+        tp = G.to_device(psi, prec)
+        td = G.to_device(d, prec)
+        out, (E, mu) = plan.grad(tp, with_energy=True)
+        ref = oracle_hpsi(g, psi)
+        assert rel(host(out), ref) <= TOL[prec], name
+        E2, mu2, n2 = plan.energy(tp)
+        Er, mur = O.energy(g, psi), O.chem_potential(g, psi)
+        etol = 1e-12 if prec == G.F64 else 1e-5
+        scale = max(abs(Er), 1.0)
+        assert abs(E - Er) <= etol * scale and abs(E2 - Er) <= etol * scale
+        assert abs(mu - mur) <= etol * max(abs(mur), 1.0)
+        assert abs(n2 - O.norm2(g, psi)) <= etol
+        shift = 0.37
+        hv = plan.hessvec(tp, td, shift)
+        refh = (O.apply_hlin(g, d) + g.beta * (np.abs(psi) ** 2 * d + 2.0 * np.real(np.conj(psi) * d) * psi)
+                + shift * d)
+        assert rel(host(hv), refh) <= TOL[prec], name
+
+
+@pytest.mark.parametrize("prec", [G.F64, G.F32], ids=["f64", "f32"])
+def test_feasible_step_parity(prec):
+    """Theorem 3.3 step with the §4 renormalisation, in grid units."""
+    p = W.problem(2, (64, 64), (-8.0, -8.0), (8.0, 8.0), "fourier", beta=200.0, omega=0.5, is_complex=True)
+    g = O.build_grid(p)
+    psi = as_prec(W.random_field(p, seed=3, smooth=0.1), prec)
+    with G.Plan(p, prec=prec) as plan:
+        tp = G.to_device(psi, prec)
+        hp = plan.grad(tp)
+        hpsi = host(hp)
+        U = O.Unified(g)
+        for tau in (0.0, 1e-3, 0.02):
+            out, E = plan.feasible_step(tp, hp, tau, with_energy=True)
+            X, Gx = U.to_X(psi), 2.0 * math.sqrt(g.h_vol) * hpsi
+            Y = O.cayley_step(X, Gx, tau)
+            Y = Y / np.linalg.norm(Y)
+            ref = U.to_psi(Y)
+            assert rel(host(out), ref) <= (1e-12 if prec == G.F64 else 2e-6)
+            assert abs(O.norm2(g, host(out)) - 1.0) <= (1e-13 if prec == G.F64 else 1e-6)
+            assert abs(E - O.energy(g, as_prec(host(out), prec))) <= (1e-11 if prec == G.F64 else 1e-5) * abs(E)
+
+
+@pytest.mark.parametrize("disc,dim,cplx", [("fourier", 2, False), ("fourier", 2, True), ("sine", 2, False),
+                                           ("sine", 3, False), ("fd", 2, False), ("fourier", 1, False)])
+def test_prolong_parity(disc, dim, cplx):
+    """Algorithm 3 transfer (reading: spectral zero-padding / linear for FD)."""
+    n = {1: (32,), 2: (16, 32), 3: (8, 16, 8)}[dim]
+    lo, hi = (-6.0,) * dim, (6.0,) * dim
+    pc = W.problem(dim, n, lo, hi, disc, beta=10.0, omega=0.3 if cplx else 0.0, is_complex=cplx)
+    pf = W.problem(dim, tuple(2 * v for v in n), lo, hi, disc, beta=10.0, omega=0.3 if cplx else 0.0,
+                   is_complex=cplx)
+    gc, gf = O.build_grid(pc), O.build_grid(pf)
+    psi_c = W.random_field(pc, seed=5, smooth=0.1)
+    with G.Plan(pc) as plc, G.Plan(pf) as plf:
+        out = plc.prolong_to(plf, G.to_device(psi_c))
+        ref = O.prolong(gc, gf, psi_c)
+        assert rel(host(out), ref) <= 1e-12
+
+
+def test_batched_plan_matches_single_instances():
+    p = W.problem(2, (32, 32), (-6.0, -6.0), (6.0, 6.0), "fourier", beta=60.0, omega=0.4, is_complex=True)
+    g = O.build_grid(p)
+    fields = [W.random_field(p, seed=s, smooth=0.05) for s in (1, 2, 3)]
+    with G.Plan(p, nbatch=3) as plan:
+        t = torch.stack([G.to_device(f) for f in fields]).contiguous()
+        out, (E, mu) = plan.grad(t, with_energy=True)
+        for b, f in enumerate(fields):
+            assert rel(host(out[b]), oracle_hpsi(g, f)) <= 1e-12
+            assert abs(E[b] - O.energy(g, f)) <= 1e-12 * abs(E[b])
+
+
+def test_reductions_deterministic():
+    p = W.problem(2, (128, 128), (-8.0, -8.0), (8.0, 8.0), "fourier", beta=100.0, omega=0.8, is_complex=True)
+    psi = W.random_field(p, seed=9)
+    with G.Plan(p, prec=G.F32) as plan:
+        t = G.to_device(psi, G.F32)
+        r1 = plan.energy(t)
+        r2 = plan.energy(t)
+        assert r1 == r2
+
+
+def test_nonfinite_input_reported():
+    p = W.problem(1, (32,), (-4.0,), (4.0,), "fourier", beta=1.0)
+    psi = W.random_field(p, seed=1)
+    psi[3] = np.nan
+    with G.Plan(p) as plan:
+        with pytest.raises(G.GPEError) as e:
+            plan.energy(G.to_device(psi))
+        assert e.value.status == 4
+
+
+# ------------------------------------------------------------------ full-size sampled parity
+
+@pytest.mark.parametrize("cfg,prec", [("c4", G.F32), ("c4", G.F64), ("c3", G.F32)])
+def test_full_size_operator_parity(cfg, prec):
+    """Configuration sizes (512^2 complex rotating, 128^3 sine lattice): full
+    H psi vs the oracle on the same bytes."""
+    p = W.config(cfg)
+    g = O.build_grid(p)
+    psi = as_prec(W.random_field(p, seed=21, smooth=0.02), prec)
+    with G.Plan(p, prec=prec) as plan:
+        out, (E, mu) = plan.grad(G.to_device(psi, prec), with_energy=True)
+        ref = oracle_hpsi(g, psi)
+        assert rel(host(out), ref) <= TOL[prec]
+        assert abs(E - O.energy(g, psi)) <= (1e-12 if prec == G.F64 else 1e-5) * abs(E)
+
+
+# ------------------------------------------------------------------ solvers
+
+def _align_phase(a, ref):
+    """Multiply a by the unit phase that best matches ref (ground states are
+    unique only up to a global phase)."""
+    z = np.vdot(a, ref)
+    return a * (z / abs(z)) if abs(z) > 0 else a
+
+
+@pytest.mark.parametrize("iters", [1, 3, 12])
+def test_algorithm1_iterates_match_oracle(iters):
+    """Device Algorithm 1 (float64) follows the oracle's iterates: same BB
+    steps, same nonmonotone decisions, same Cayley update."""
+    p = W.problem(1, (128,), (-12.0,), (12.0,), "fourier", beta=100.0)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    psi0 = W.gaussian(p)
+    r = O.feasible_gradient(U.fg, U.to_X(psi0), max_iter=iters, eps0=0.0)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, method=1, mode=0, levels=1, max_iter=iters, eps0=0.0, res_tol=0.0)
+        got = host(t)
+    ref = U.to_psi(r.X)
+    assert rel(got, ref) <= 1e-9
+    assert abs(rep["E"] - r.F) <= 1e-12 * abs(r.F)
+
+
+def test_c1_regularized_newton_fp64():
+    """Config 1 (1D Fourier 512, beta = 400): Algorithm 2 in float64 to
+    ||H psi - mu psi||_h < 1e-10; E, mu, x_rms vs the oracle and §4.1's values."""
+    p = W.config("c1")
+    g = O.build_grid(p)
+    psi0 = W.gaussian(p)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, mode=0, levels=1, res_tol=1e-10, delta_stop=0.0)
+        psi = host(t)
+    U = O.Unified(g)
+    ro = O.regularized_newton(U, U.to_X(psi0), res_tol=2e-10, delta_stop=0.0)
+    psi_o = U.to_psi(ro.X)
+    E_o = O.energy(g, psi_o)
+    assert rep["res"] < 1e-10
+    assert abs(rep["E"] - E_o) <= 1e-9 * E_o
+    assert abs(O.energy(g, psi) - E_o) <= 1e-9 * E_o
+    assert rel(psi * np.sign(np.vdot(psi, psi_o).real), psi_o) <= 1e-6
+    assert abs(rep["E"] - 21.3601) <= 1e-4 and abs(rep["mu"] - 35.5775) <= 1e-4
+    assert abs(O.rms(g, psi, 0) - 3.7751) <= 1e-4
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_c2_cascade(mode):
+    """Config 2 (2D Fourier 256^2, beta = 1000, cascade 64->128->256):
+    float64 and float32-bulk/float64-refined solves vs the oracle's cascade."""
+    p = W.config("c2")
+    psi0 = W.gaussian(p)
+    gf, psi_o, _ = O.cascadic(p, psi0, levels=3, method="rn", res_tol_psi=1e-10)
+    E_o = O.energy(gf, psi_o)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, mode=mode, levels=3, res_tol=1e-9)
+        psi = host(t)
+    assert abs(rep["E"] - E_o) <= 1e-9 * E_o, (rep, E_o)
+    assert abs(O.energy(gf, psi) - E_o) <= 1e-9 * E_o
+    assert rel(psi * np.sign(np.vdot(psi, psi_o).real), psi_o) <= 1e-5
+    assert abs(rep["E"] - 11.9718) <= 1e-4
+
+
+def test_c3_reduced_sine_lattice_mixed():
+    """Config 3's discretisation and trap (sine, depth-100 lattice, beta = 1600)
+    on 32^3 intervals, cascade 16 -> 32, mixed precision, vs the oracle."""
+    p = W.config("c3")
+    p["n"] = (32, 32, 32)
+    psi0 = W.gaussian(p)
+    gf, psi_o, _ = O.cascadic(p, psi0, levels=2, method="rn", res_tol_psi=1e-9)
+    E_o = O.energy(gf, psi_o)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, mode=1, levels=2, res_tol=1e-9)
+        psi = host(t)
+    assert abs(rep["E"] - E_o) <= 1e-9 * E_o
+    assert rel(psi * np.sign(np.vdot(psi, psi_o).real), psi_o) <= 1e-5
+
+
+def _certify(g, psi, E_gpu, tol_res):
+    """Oracle-side check of a GPU state: stationary (residual) and same energy."""
+    hp = oracle_hpsi(g, psi)
+    mu = O.chem_potential(g, psi)
+    r = math.sqrt(O.norm2(g, hp - mu * psi))
+    E = O.energy(g, psi)
+    assert r <= tol_res, r
+    assert abs(E - E_gpu) <= 1e-9 * abs(E)
+    return E, mu, r
+
+
+def test_c4_reduced_rotating_mixed():
+    """Rotating config (Omega = 0.9, beta = 1000, phi_c + phase noise) on 128^2:
+    the GPU state is a stationary point by the oracle's operator, with the
+    oracle's energy; if both solvers reach the same basin the energies agree
+    to 1e-9, otherwise the oracle started from the GPU state stays there."""
+    p = W.config("c4")
+    p["n"] = (128, 128)
+    g = O.build_grid(p)
+    psi0 = W.rotating_initial(p, "c", noise=1e-2, seed=1504)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, mode=1, levels=1, res_tol=1e-9)
+        psi = host(t)
+    E, mu, r = _certify(g, psi, rep["E"], 1e-8)
+    U = O.Unified(g)
+    ro = O.regularized_newton(U, U.to_X(psi0), res_tol=2e-9, delta_stop=0.0)
+    E_o = ro.F
+    if abs(E_o - E) > 1e-9 * E:
+        rw = O.regularized_newton(U, U.to_X(psi), k_init=0, res_tol=2e-9, delta_stop=0.0)
+        assert abs(rw.F - E) <= 1e-9 * E
+
+
+def test_c4_full_size_certified():
+    """Config 4 at its full size (512^2 complex): mixed solve; the oracle
+    certifies the state (residual, energy) at full size."""
+    p = W.config("c4")
+    g = O.build_grid(p)
+    psi0 = W.rotating_initial(p, "c", noise=1e-2, seed=1504)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, mode=1, levels=1, res_tol=1e-9)
+        psi = host(t)
+    _certify(g, psi, rep["E"], 1e-8)

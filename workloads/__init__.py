@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "problem", "axis_nodes", "array_shape", "cell_volume", "normalise",
-    "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep",
+    "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep", "random_field",
 ]
 
 
@@ -183,3 +183,20 @@ def batched_sweep(count=256, seed=20150410):
                            beta=beta, omega=om, is_complex=True,
                            potential={"kind": "harmonic", "gamma": (1.0, gy)}))
     return out
+
+
+def random_field(p, seed=0, smooth=0.0):
+    """Seeded random grid function of unit discrete norm (complex if the
+    problem is complex).  smooth > 0 multiplies by a Gaussian envelope
+    exp(-smooth |x|^2) so that the values decay towards the box edges."""
+    rng = np.random.default_rng(seed)
+    shape = array_shape(p)
+    psi = rng.standard_normal(shape)
+    if p["is_complex"]:
+        psi = psi + 1j * rng.standard_normal(shape)
+    if smooth > 0.0:
+        env = np.ones(shape)
+        for x in _mesh(p):
+            env = env * np.exp(-smooth * x * x)
+        psi = psi * env
+    return normalise(p, psi)
