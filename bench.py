@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: time to ground state of the 2D non-rotating GPE (Fourier 256^2
+on [-16,16]^2, V = (x^2+y^2)/2, beta = 1000, Gaussian initial guess, cascadic
+multigrid 64^2 -> 128^2 -> 256^2) with the float32-bulk / float64-refined
+regularized Newton solver, against the plain float64 GPU solver, plus the
+H psi apply throughput of the operator kernels against the HBM roofline.
+
+One step = one complete ground-state solve (Algorithm 3 around Algorithm 2,
+every operator application, Cayley step, reduction and ratio test on the GPU)
+from the initial guess resident in HBM.  Stopping rule: ||H psi - mu psi||_h
+<= 1e-9, which puts |E - E_oracle| far below 1e-9 E (checked against the FP64
+oracle's ground state in the CPU-baseline leg).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own replica (the solve does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-ground-state at ΔE≤1e-9, mixed vs FP64 on GB300; "
+          "Hψ apply GB/s vs peak")
+WORKLOAD = ("2D non-rotating GPE, Fourier 256^2 on [-16,16]^2, V=(x^2+y^2)/2, beta=1000, real psi, "
+            "Gaussian init, cascade 64^2->128^2->256^2, float32 bulk + float64 refinement "
+            "to ||H psi - mu psi||_h <= 1e-9")
+RES_TOL = 1e-9
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per grid point of one operator application, by the kind of
+# its final pass (read the operands the method needs once, write the result
+# once): H psi apply (read X, write G); an Algorithm 1 iteration with the
+# Cayley step formed in the first pass's load (read X_c, G_c, write G_new, plus
+# the trial point Y); the ratio pass (read Z, X^k, G^k).  Per real number: 4 B
+# (float32) or 8 B (float64); complex doubles it.
+ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# --------------------------------------------------------------------------- oracle legs
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import oracle as O, workloads as W
+p = W.config("c2")
+psi0 = W.gaussian(p)
+t_end = time.perf_counter() + {budget}
+times, E = [], None
+while True:
+    t0 = time.perf_counter()
+    g, psi, res = O.cascadic(p, psi0, levels=3, method="rn", res_tol_psi={res_tol})
+    times.append(time.perf_counter() - t0)
+    E = O.energy(g, psi)
+    if len(times) >= {max_runs} or time.perf_counter() > t_end:
+        break
+print(json.dumps({{"times": times, "E": E, "mu": O.chem_potential(g, psi)}}))
+"""
+
+
+def run_oracle(budget_s, max_runs, threads=1):
+    """The FP64 oracle's cascade solve of the same workload on the host cores,
+    in a subprocess with BLAS pinned to `threads` threads."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    code = ORACLE_SNIPPET.format(root=ROOT, budget=budget_s, res_tol=RES_TOL, max_runs=max_runs)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per_step_budget = 60.0
+    times = []
+    E = None
+    for i in range(args.warmup + args.steps):
+        r = run_oracle(per_step_budget, 1)
+        if i >= args.warmup:
+            times.append(r["times"][0])
+        E = r["E"]
+    t = statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": t, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "rank 0 only (host oracle)"},
+        "cpu_baseline": {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": "one full FP64 oracle cascade solve of the workload per step (numpy, dense DFT matrices, BLAS pinned to 1 thread)"},
+        "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "E": E,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+def roofline_from_profile(prof, peaks):
+    """Dominant operator application of the profiled solve: group the pass
+    kernels by (precision, complexity, grid size), take the group with the
+    largest total time, count its applications by its final-pass launches."""
+    groups = {}
+    for name, (n, ms) in prof.items():
+        if "@" not in name:
+            continue
+        kern, size = name.split("@")
+        parts = kern.split("_")             # pass_f32_r_W
+        if parts[0] not in ("pass", "fd", "step"):
+            continue
+        key = (parts[1], parts[2], int(size))
+        g = groups.setdefault(key, {"ms": 0.0, "final": {}, "kernels": {}})
+        g["ms"] += ms
+        g["kernels"][kern] = (n, ms)
+        if len(parts) > 3 and parts[3] != "acc":
+            g["final"][parts[3]] = g["final"].get(parts[3], 0) + n
+    if not groups:
+        return None
+    key = max(groups, key=lambda k: groups[k]["ms"])
+    g = groups[key]
+    prec, cplx, M = key
+    napp = sum(g["final"].values())
+    kind = max(g["final"], key=lambda k: g["final"][k]) if g["final"] else "grad"
+    real_bytes = 4 if prec == "f32" else 8
+    per_point = sum(ALG_REALS_PER_POINT[k] * c for k, c in g["final"].items()) / max(napp, 1)
+    per_point *= real_bytes * (2 if cplx == "c" else 1)
+    t_app = g["ms"] / max(napp, 1) * 1e-3
+    achieved = per_point * M / t_app / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"operator application {prec}/{cplx}/M={M} ({kind} final pass)",
+            "launches_per_application": sum(n for n, _ in g["kernels"].values()) / max(napp, 1),
+            "us_per_application": t_app * 1e6, "alg_bytes_per_point": per_point,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+
+
+def happly_throughput(G, torch, W, peaks, reps=20):
+    """H psi apply on inputs far above L2: 64 instances of the 512^2 rotating
+    grid in complex64 (256 MiB read+write per apply)."""
+    p = W.config("c4")
+    nb = 64
+    plan = G.Plan(p, nbatch=nb, prec=G.F32)
+    psi = plan.empty()
+    psi.real.normal_()
+    psi.imag.normal_()
+    psi.mul_(1e-2)
+    out = plan.empty()
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        plan.grad(psi, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        plan.grad(psi, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    M = plan.M * nb
+    alg = 16.0 * M                 # read psi (8 B) + write H psi (8 B) per point, complex64
+    achieved = alg / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    plan.close()
+    return {"workload": "H psi apply, 64 x 512^2 complex64 rotating (Omega=0.9), float32",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "us_per_apply": ms * 1e3, "alg_bytes_per_apply": alg}
+
+
+def our_arm(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import workloads as W
+    import paper_1504_02891_gb300 as G
+    G.load()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = W.config("c2")
+    psi0 = W.gaussian(p)
+    plan = G.Plan(p, prec=G.F64)
+    init = G.to_device(psi0)
+    work = torch.empty_like(init)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    opts_mixed = dict(mode=1, levels=3, res_tol=RES_TOL)
+    opts_fp64 = dict(mode=0, levels=3, res_tol=RES_TOL)
+
+    def step(opts):
+        work.copy_(init)
+        return plan.solve(work, **opts)
+
+    def timed(opts, k):
+        times, reps = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(k):
+            flush.fill_(1.0)                      # evict L2 between steps (untimed)
+            torch.cuda.synchronize()
+            e0.record(st)
+            rep = step(opts)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            reps.append(rep)
+        return times, reps
+
+    for _ in range(args.warmup):
+        step(opts_mixed)
+        step(opts_fp64)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler()
+    time.sleep(0.3)
+    barrier()
+    l0 = G.kernel_launches()
+    t_mixed, reps_mixed = timed(opts_mixed, args.steps)
+    l1 = G.kernel_launches()
+    barrier()
+    t_fp64, reps_fp64 = timed(opts_fp64, max(3, args.steps // 2))
+    barrier()
+    clk = clocks.stop(gpu_index=local)
+
+    ms_mixed = statistics.mean(t_mixed)
+    ms_fp64 = statistics.mean(t_fp64)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_mixed, ms_fp64], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_fp64 = float(tt[0]), float(tt[1])
+
+    # end to end through the public API with host buffers (pinned)
+    h_init = torch.from_numpy(np.ascontiguousarray(psi0)).pin_memory()
+    h_out = torch.empty_like(h_init).pin_memory()
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        work.copy_(h_init, non_blocking=True)
+        plan.solve(work, **opts_mixed)
+        h_out.copy_(work, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    nbytes = h_init.numel() * h_init.element_size()
+
+    # profiled solve (CUDA events around every launch, graphs off) -> roofline
+    G.profile_enable(True)
+    step(opts_mixed)
+    torch.cuda.synchronize()
+    prof = G.profile_summary()
+    G.profile_enable(False)
+    roof = roofline_from_profile(prof, peaks)
+    happly = happly_throughput(G, torch, W, peaks)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    dE = None
+    if not args.no_cpu_baseline:
+        try:
+            r = run_oracle(args.cpu_seconds, 50, threads=1)
+            tcpu = statistics.mean(r["times"])
+            cpu = {"value": tcpu, "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": f"{len(r['times'])} complete FP64 oracle cascade solves of the same workload "
+                             "(numpy, dense DFT matrices, BLAS pinned to 1 thread)"}
+            dE = abs(reps_mixed[-1]["E"] - r["E"]) / abs(r["E"])
+        except Exception as e:  # reported, never fatal
+            cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    rep = reps_mixed[-1]
+    line = {
+        "metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [256, 256], "levels": 3, "beta": 1000.0,
+                   "l2": "flushed between steps (256 MiB write, untimed); each step timed with CUDA events",
+                   "parallelism": f"replicas x{world} (no data-path collective)"},
+        "fp64_time_s": ms_fp64 / 1e3, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
+        "throughput": {"value": world * 1e3 / ms_mixed, "unit": "ground states/s"},
+        "E": rep["E"], "mu": rep["mu"], "res": rep["res"], "delta_E_rel_vs_oracle": dE,
+        "solver": {k: rep[k] for k in ("outer_f32", "outer_f64", "inner_f32", "inner_f64", "nfe", "ms_f32", "ms_f64")},
+        "roofline": roof, "happly": happly,
+        "cpu_baseline": cpu,
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int((l1 - l0) / max(args.steps, 1)) * args.steps,
+        "clocks": clk,
+        "profile": {k: [n, round(ms, 4)] for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,8 +140,9 @@ gpe_status gpe_prolong(gpe_plan coarse, gpe_plan fine, const void* psi_c, void* 
  * given in brackets. */
 typedef struct {
   int levels;         /* cascade levels of Algorithm 3, >= 1 (coarsest = n >> (levels-1)) [1] */
-  int mode;           /* 0: float64 throughout; 1: float32 bulk then float64
-                         refinement; 2: float32 only                           [1] */
+  int mode;           /* 0: float64 throughout; 1: float32 bulk (Algorithm 1 on
+                         every level) then float64 regularized Newton on the
+                         finest level; 2: float32 only                         [1] */
   int method;         /* 0: Algorithm 2 (regularized Newton); 1: Algorithm 1    [0] */
   int k_init;         /* Algorithm 1 warm-start iterations in Algorithm 2       [100] */
   int k_sub;          /* Algorithm 1 iterations per subproblem (Eq. tr-sub)     [200] */
@@ -151,8 +152,9 @@ typedef struct {
   double delta_stop;  /* Eq. crit2 tolerance on accepted steps (Algorithm 2)    [1e-8] */
   double res_tol;     /* stop when ||H psi - mu psi||_h <= res_tol (0 = off)    [1e-9] */
   double delta0;      /* initial regularisation (unified variables)             [1.0] */
-  double switch_rel;  /* mode 1: leave float32 once ||H psi - mu psi||_h <=
-                         switch_rel * mu or float32 stagnates                   [2e-6] */
+  double switch_rel;  /* modes 1, 2: the float32 bulk (Algorithm 1 on every
+                         level) stops once ||A(X)X|| <= switch_rel * |X^*G|, or
+                         when 40 steps bring no new smallest residual          [1e-6] */
   int chunk;          /* Algorithm 1 iterations queued between host checks      [16] */
   int use_graphs;     /* capture the queued iterations in CUDA graphs           [1] */
 } gpe_solve_opts;
@@ -178,6 +180,20 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
  * stopping rules (the state is still written). */
 gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
                              gpe_solve_report* report);
+
+/* Instrumentation (the paper has no counterpart; used by the benchmark).
+ * gpe_kernel_launches: kernels this process has launched through libgpe so far
+ *   (a CUDA-graph launch counts each of its kernel nodes).
+ * gpe_profile_enable(1): from now on record a pair of CUDA events on the
+ *   launching stream around every kernel libgpe launches outside stream
+ *   capture; gpe_rnewton_solve then runs without CUDA graphs so that every
+ *   launch is recorded.  gpe_profile_enable(0) stops and discards the records.
+ * gpe_profile_summary: synchronises the recorded events and writes a JSON
+ *   object {"kernel-name": [launches, total_ms], ...} into buf (NUL
+ *   terminated, truncated to buflen).  GPE_EINVAL if buf is NULL. */
+int64_t gpe_kernel_launches(void);
+gpe_status gpe_profile_enable(int on);
+gpe_status gpe_profile_summary(char* buf, int buflen);
 
 #ifdef __cplusplus
 }

@@ -115,6 +115,9 @@ def load():
         "gpe_prolong": ([vp, vp, vp, vp], ip),
         "gpe_solve_opts_default": ([C.POINTER(SolveOpts)], ip),
         "gpe_rnewton_solve": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveReport)], ip),
+        "gpe_kernel_launches": ([], C.c_int64),
+        "gpe_profile_enable": ([ip], ip),
+        "gpe_profile_summary": ([C.c_char_p, ip], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -266,6 +269,24 @@ class Plan:
         r = SolveReport()
         _check(load().gpe_rnewton_solve(self.handle, _ptr(psi), C.byref(o), C.byref(r)), allow=(5,))
         return r.as_dict()
+
+
+def kernel_launches():
+    """Kernels launched through libgpe by this process so far."""
+    return int(load().gpe_kernel_launches())
+
+
+def profile_enable(on=True):
+    _check(load().gpe_profile_enable(1 if on else 0))
+
+
+def profile_summary():
+    """{kernel-name: (launches, total_ms)} of the launches recorded since
+    profile_enable(True)."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(load().gpe_profile_summary(buf, len(buf)))
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
 def default_opts():

@@ -102,6 +102,17 @@ gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int e
 
 void destroy_solver_cache(void* cache);
 
+// Instrumentation: launch counting and optional per-kernel CUDA-event timing.
+void instr_count(long long n);
+bool prof_enabled();
+struct ProfScope {
+  int slot = -1;
+  cudaStream_t st = nullptr;
+  ProfScope(const char* name, cudaStream_t s);   // counts the launch unless the stream is capturing
+  ~ProfScope();
+};
+const char* kernel_name(const char* base, int f64, int cplx, int epi, long long points = -1);
+
 inline size_t elem_size(int prec, int cplx) { return (prec == GPE_F64 ? 8 : 4) * (cplx ? 2 : 1); }
 
 }  // namespace gpe

@@ -22,7 +22,8 @@ template <typename T> struct C2t;
 template <> struct C2t<float> { using type = float2; };
 template <> struct C2t<double> { using type = double2; };
 
-constexpr int NTHREADS = 256;
+constexpr int NTHREADS = 256;  // largest block size
+constexpr int MAXLB = 128;     // data lines per tile
 constexpr int NQ = 14;         // reduction slots per launch and instance
 
 // Reduction slots of the solver's evaluation passes (EPI_F / EPI_W).
@@ -59,11 +60,15 @@ struct Alg1Ctl {
   // slot state
   int cur, prev, trial, has_cur, done, status, phase, pad0;
   double theta_c;      // theta of the current point (used by the passes)
+  double theta_hint;   // before the first point is accepted: a nearby theta
+                       // (the projected-gradient norm is formed relative to it)
   // iteration state
   int k, m, nfe, accepted_last;
   double tau, C, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;
   double a, b, s;      // Cayley step coefficients of the next trial
   double res;          // ||A(X)X||_2 of the current point
+  double best_res;     // smallest res seen (stagnation test)
+  int k_best, stall_iters;   // stop after stall_iters accepted steps without a new best (0 = off)
 };
 
 // Outer state of Algorithm 2 (ratio test), written by the ratio pass.
@@ -83,8 +88,11 @@ struct PassGeom {
   long long ostride;    // axes 1,2: stride of the outer index
   int F, logF;          // FFT length
   int odd_ext;          // sine grid: odd extension to 2N
-  int LB;               // data lines per tile
+  int LB;               // data lines per tile (power of two, <= MAXLB)
+  int logLB;
   int LC;               // complex lines per tile
+  int tpl, ltpl;        // axis 0: threads per line (power of two) and its log2
+  int nthreads;         // block size
   int tiles;            // tiles per instance
   int xt;               // axes 1,2: tiles along x
   const typename C2t<T>::type* tw;  // e^{-2 pi i k / F}

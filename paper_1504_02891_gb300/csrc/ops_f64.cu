@@ -7,6 +7,7 @@ GPE_INSTANTIATE(double)
 namespace gpe {
 template <typename Ti, typename To>
 gpe_status launch_convert(const Ti* in, To* out, long long n, double scale, cudaStream_t st) {
+  ProfScope ps(kernel_name("convert", sizeof(To) == 8, 0, -1), st);
   k_convert<Ti, To><<<ew_blocks(n), NTHREADS, 0, st>>>(in, out, n, scale);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
@@ -17,12 +18,14 @@ template gpe_status launch_convert<float, float>(const float*, float*, long long
 template gpe_status launch_convert<double, double>(const double*, double*, long long, double, cudaStream_t);
 
 gpe_status launch_step_coef(const double* mom, int nbatch, double h, double tau, double* coef, cudaStream_t st) {
+  ProfScope ps("step_coef", st);
   k_step_coef<<<(nbatch + 127) / 128, 128, 0, st>>>(mom, nbatch, h, tau, coef);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
 }
 
 gpe_status launch_norm_coef(const double* mom, int nbatch, double h, double* coef, cudaStream_t st) {
+  ProfScope ps("norm_coef", st);
   k_norm_coef<<<(nbatch + 127) / 128, 128, 0, st>>>(mom, nbatch, h, coef);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;

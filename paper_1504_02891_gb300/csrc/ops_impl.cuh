@@ -226,7 +226,7 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
     return;
   }
   const double thY = YG / nY;
-  const double dth = thY - (c->has_cur ? c->theta_c : 0.0);
+  const double dth = thY - (c->has_cur ? c->theta_c : c->theta_hint);
   double PPn = r[Q_Q] - 2.0 * dth * r[Q_QY] + dth * dth * nY;
   if (PPn < 0.0) PPn = 0.0;
   const double SS = r[Q_SS];
@@ -276,6 +276,14 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
   c->accepted_last = 1;
   if (c->res_tol > 0.0 && c->res <= c->res_tol) { c->done = 1; c->status = 0; }
   if (c->res_rel > 0.0 && c->res <= c->res_rel * fabs(thY)) { c->done = 1; c->status = 0; }
+  // precision floor: no new smallest residual (by 10%) for stall_iters steps
+  if (c->phase == 1 && (c->k == 0 || c->res < 0.9 * c->best_res)) {
+    c->best_res = c->res;
+    c->k_best = c->k;
+  } else if (c->stall_iters > 0 && c->k - c->k_best >= c->stall_iters) {
+    c->done = 1;
+    c->status = 0;
+  }
   if (!c->done && c->k >= c->max_iter) { c->done = 1; c->status = 5; }
   set_coef(c);
 }
@@ -408,6 +416,8 @@ __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& 
         E.xc = (const V*)D.xs[c->cur];
         E.gc = (const V*)D.gs[c->cur];
         E.th_c = (T)c->theta_c;
+      } else {
+        E.th_c = (T)c->theta_hint;
       }
     }
   }
@@ -423,23 +433,52 @@ __device__ __forceinline__ void run_control(const PassData<T>& D) {
 }
 
 // ----------------------------------------------------------------- the axis pass
+// Visit the data elements (line l, position j, global offset) of this CTA's
+// tile with a coalesced thread mapping and no integer division: axis-0 lines
+// are contiguous (tpl threads per line); strided lines are read as LB
+// consecutive x positions per row.
+template <typename T, typename Fn>
+__device__ __forceinline__ void visit_tile(const PassGeom<T>& G, const long long* s_off, Fn&& fn) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  if (G.axis == 0) {
+    const int lps = nt >> G.ltpl;
+    for (int l = tid >> G.ltpl; l < G.LB; l += lps) {
+      const long long off = s_off[l];
+      if (off < 0) continue;
+      for (int j = tid & (G.tpl - 1); j < G.len; j += G.tpl) fn(l, j, off + j);
+    }
+  } else {
+    const int nval = G.LB * G.len;
+    for (int f = tid; f < nval; f += nt) {
+      const int l = f & (G.LB - 1);
+      const int j = f >> G.logLB;
+      const long long off = s_off[l];
+      if (off < 0) continue;
+      fn(l, j, off + (long long)j * G.stride);
+    }
+  }
+}
+
 template <typename T, bool CPLX, int EPI>
 __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D) {
   using C = typename C2t<T>::type;
   using V = typename VT<T, CPLX>::V;
   if (D.ctl && D.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_off[MAXLB];
+  __shared__ T s_rc[MAXLB];
   C* buf0 = reinterpret_cast<C*>(smem_raw);
   C* buf1 = buf0 + G.LC * G.F;
   const int inst = blockIdx.x / G.tiles;
   const int tile = blockIdx.x - inst * G.tiles;
   const int F = G.F;
+  const int nt = blockDim.x, tid = threadIdx.x;
 
   const V* xin = (const V*)D.x;
   V* yst = nullptr;
   const V* xcur = nullptr;
   const V* gcur = nullptr;
-  T sa = 0, sb = 0, ss = 0;
+  T sa = 0, sb = 0;
   if (D.use_slots) {
     const Alg1Ctl* c = D.ctl;
     xin = (const V*)D.xs[c->trial];
@@ -452,20 +491,18 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
     }
   }
   const V* xsub = (const V*)D.xsub;
-  (void)ss;
 
-  for (int i = threadIdx.x; i < G.LC * F; i += blockDim.x) buf0[i] = mk<C>(0.0, 0.0);
-  __syncthreads();
-
-  const int nval = G.LB * G.len;
-  for (int f = threadIdx.x; f < nval; f += blockDim.x) {
-    int l, j;
-    if (G.axis == 0) { l = f / G.len; j = f - l * G.len; }
-    else { j = f / G.LB; l = f - j * G.LB; }
+  for (int l = tid; l < G.LB; l += nt) {
     long long b;
     int ri;
-    if (!line_base(G, inst, tile, l, b, ri)) continue;
-    const long long gi = b + (long long)j * G.stride;
+    const bool ok = line_base(G, inst, tile, l, b, ri);
+    s_off[l] = ok ? b : -1;
+    if (G.rcoord) s_rc[l] = G.rcoord[ok ? ri : 0];
+  }
+  for (int i = tid; i < G.LC * F; i += nt) buf0[i] = mk<C>(0.0, 0.0);
+  __syncthreads();
+
+  visit_tile(G, s_off, [&](int l, int j, long long gi) {
     V v;
     if (yst) {
       v = sa * xcur[gi] + sb * gcur[gi];
@@ -485,23 +522,17 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
       row[2 * m + comp] = v;
       if (G.odd_ext) row[2 * (F - m) + comp] = -v;
     }
-  }
+  });
   __syncthreads();
 
   C* r = fft_lines<C>(buf0, buf1, F, G.LC, G.tw);
   // symbol multiply; the conjugation turns the next forward FFT into the inverse
-  for (int t = threadIdx.x; t < G.LC * F; t += blockDim.x) {
+  for (int t = tid; t < G.LC * F; t += nt) {
     const int c = t >> G.logF;
     const int m = t & (F - 1);
     const T lm = G.lam[m];
     T sym = G.c2 * lm * lm;
-    if (G.rcoord) {
-      long long bb;
-      int ri = 0;
-      line_base(G, inst, tile, c, bb, ri);
-      if (G.axis == 1 && ri >= G.n0) ri = G.n0 - 1;
-      sym += G.c1 * G.rcoord[ri] * lm;
-    }
+    if (G.rcoord) sym += G.c1 * s_rc[c] * lm;
     C v = r[t];
     v.x = sym * v.x;
     v.y = -sym * v.y;
@@ -516,14 +547,8 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
   const V* accin = (const V*)D.acc_in;
-  for (int f = threadIdx.x; f < nval; f += blockDim.x) {
-    int l, j;
-    if (G.axis == 0) { l = f / G.len; j = f - l * G.len; }
-    else { j = f / G.LB; l = f - j * G.LB; }
-    long long b;
-    int ri;
-    if (!line_base(G, inst, tile, l, b, ri)) continue;
-    const long long gi = b + (long long)j * G.stride;
+  const long long ibase = inst * G.M;
+  visit_tile(G, s_off, [&](int l, int j, long long gi) {
     const int m = G.odd_ext ? j + 1 : j;
     V kin;
     if constexpr (CPLX) {
@@ -538,7 +563,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
       V a = kin;
       if (accin) a = accin[gi] + a;
       ((V*)D.out)[gi] = a;
-      continue;
+      return;
     }
     V x;
     if (yst) x = yst[gi];
@@ -546,11 +571,10 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
       x = xin[gi];
       if (xsub) x = x - xsub[gi];
     }
-    const long long li = gi - inst * G.M;
-    V lin = kin + D.V[li] * x;
+    V lin = kin + D.V[gi - ibase] * x;
     if (accin) lin = lin + accin[gi];
     epilogue_point<T, CPLX, EPI>(E, gi, x, lin, acc);
-  }
+  });
   if (EPI == EPI_ACC || EPI == EPI_HESS || D.nq == 0) return;
   if (reduce_partials(acc, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
 }
@@ -712,9 +736,12 @@ __global__ void k_convert(const Ti* in, To* out, long long n, double scale) {
     out[i] = (To)((double)in[i] * scale);
 }
 
-// fine -> coarse: values at the coarse nodes (Algorithm 3 initial guess)
+// fine -> coarse: values at the coarse nodes (Algorithm 3 initial guess).  The
+// fine mesh is r = 2^k times finer; coarse index i sits at fine index r*i
+// (periodic grids, node 0 shared) or r*(i+1)-1 (interior nodes of Dirichlet
+// grids).
 template <typename T, bool CPLX>
-__global__ void k_inject(const void* fv, void* cv, int dim, int f0, int f1, int c0, int c1, int c2, int off,
+__global__ void k_inject(const void* fv, void* cv, int dim, int f0, int f1, int c0, int c1, int r, int dirichlet,
                          long long Mf, long long Mc, int nbatch) {
   using V = typename VT<T, CPLX>::V;
   const V* f = (const V*)fv;
@@ -724,14 +751,14 @@ __global__ void k_inject(const void* fv, void* cv, int dim, int f0, int f1, int 
     const int b = (int)(i / Mc);
     const long long li = i - b * Mc;
     const int i0 = (int)(li % c0);
-    const long long r = li / c0;
-    const int i1 = (int)(r % c1);
-    const int i2 = (int)(r / c1);
-    const long long j0 = 2LL * i0 + off;
-    const long long j1 = dim >= 2 ? 2LL * i1 + off : 0;
-    const long long j2 = dim >= 3 ? 2LL * i2 + off : 0;
+    const long long rr = li / c0;
+    const int i1 = (int)(rr % c1);
+    const int i2 = (int)(rr / c1);
+    auto fine = [&](int ic) -> long long { return dirichlet ? (long long)r * (ic + 1) - 1 : (long long)r * ic; };
+    const long long j0 = fine(i0);
+    const long long j1 = dim >= 2 ? fine(i1) : 0;
+    const long long j2 = dim >= 3 ? fine(i2) : 0;
     c[i] = f[b * Mf + (j2 * f1 + j1) * f0 + j0];
-    (void)c2;
   }
 }
 

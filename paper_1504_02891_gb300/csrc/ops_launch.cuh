@@ -44,21 +44,25 @@ static PassGeom<T> make_geom(int axis, const int ext[3], int F, int Fbuf, int od
   G.logF = ilog2(F);
   G.odd_ext = odd_ext;
   const int budget = sizeof(T) == 4 ? 4096 : 2048;   // complex elements per buffer
-  const int lc_max = std::max(1, budget / Fbuf);
+  const int lc_cap = cplx ? MAXLB : MAXLB / 2;
+  const int lc_max = std::max(1, std::min(budget / Fbuf, lc_cap));
   long long lines = axis == 0 ? (long long)ext[1] * ext[2] : (long long)ext[0] * (axis == 1 ? ext[2] : ext[1]);
   long long tot = lines * nbatch;
   long long tot_c = cplx ? tot : (tot + 1) / 2;
+  // as many CTAs as there are SMs x 2 when the grid allows, else one line (pair) per CTA
   long long want = std::max<long long>(1, tot_c / TARGET_CTAS);
   int lc = pow2floor(std::min<long long>(want, lc_max));
   if (axis != 0) {
     const int x2 = pow2ceil(ext[0]);
+    // strided lines: read rows of >= 8 consecutive values when there is work for the whole GPU
     const int want_lb = std::min(8, x2);
     const int want_lc = cplx ? want_lb : std::max(1, want_lb / 2);
-    lc = std::max(lc, std::min(want_lc, lc_max));
+    if (tot_c >= (long long)want_lc * TARGET_CTAS) lc = std::max(lc, std::min(want_lc, lc_max));
     lc = std::min(lc, cplx ? x2 : std::max(1, x2 / 2));
   }
   G.LC = lc;
   G.LB = cplx ? lc : 2 * lc;
+  G.logLB = ilog2(G.LB);
   if (axis == 0) {
     G.tiles = (int)((lines + G.LB - 1) / G.LB);
     G.xt = 1;
@@ -66,6 +70,10 @@ static PassGeom<T> make_geom(int axis, const int ext[3], int F, int Fbuf, int od
     G.xt = (ext[0] + G.LB - 1) / G.LB;
     G.tiles = (axis == 1 ? ext[2] : ext[1]) * G.xt;
   }
+  const int work = std::max(G.LC * Fbuf / 4, G.LB * G.len);
+  G.nthreads = std::min(NTHREADS, std::max(64, pow2ceil(std::min(work, NTHREADS))));
+  G.tpl = std::min(pow2ceil(G.len), G.nthreads);
+  G.ltpl = ilog2(G.tpl);
   *blocks = G.tiles * nbatch;
   *smem = 2 * (size_t)G.LC * Fbuf * sizeof(C);
   return G;
@@ -162,7 +170,8 @@ static gpe_status launch_pass_t(const PassGeom<T>& G, int blocks, size_t smem, c
     allow_smem(k_pass<T, CPLX, EPI>, smem);
     allowed = smem;
   }
-  k_pass<T, CPLX, EPI><<<blocks, NTHREADS, smem, st>>>(G, D);
+  ProfScope ps(kernel_name("pass", sizeof(T) == 8, CPLX, EPI, G.M * (blocks / G.tiles)), st);
+  k_pass<T, CPLX, EPI><<<blocks, G.nthreads, smem, st>>>(G, D);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
 }
@@ -191,6 +200,7 @@ template <typename T>
 gpe_status launch_fd(const GridDev<T>& d, const PassData<T>& D, int cplx, int epi, cudaStream_t st) {
   const T* rx = d.coord[0];
   const T* ry = d.coord[1] ? d.coord[1] : d.coord[0];
+  ProfScope ps(kernel_name("fd", sizeof(T) == 8, cplx, epi, d.fd.M * (d.fd_blocks / d.fd.tiles)), st);
 #define GPE_FD_CASE(E)                                                                                   \
   case E:                                                                                                \
     if (cplx) k_fd<T, true, E><<<d.fd_blocks, NTHREADS, 0, st>>>(d.fd, rx, ry, D);                        \
@@ -216,6 +226,7 @@ static inline int ew_blocks(long long n) {
 
 template <typename T>
 gpe_status launch_step(void* const* xs, void* const* gs, const Alg1Ctl* ctl, long long n, int cplx, cudaStream_t st) {
+  ProfScope ps(kernel_name("step", sizeof(T) == 8, cplx, -1, n), st);
   if (cplx) k_step<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n);
   else k_step<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n);
   GPE_CUDA(cudaGetLastError());
@@ -227,6 +238,7 @@ gpe_status launch_moments(const void* x, const void* g, long long M, int nbatch,
                           cudaStream_t st) {
   const int tiles = (int)std::max<long long>(1, std::min<long long>((M + NTHREADS - 1) / NTHREADS, 512));
   if ((size_t)tiles * nbatch > sc.cap_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
+  ProfScope ps(kernel_name("moments", sizeof(T) == 8, cplx, -1), st);
   if (cplx) k_moments<T, true><<<tiles * nbatch, NTHREADS, 0, st>>>(x, g, M, tiles, sc.partials, sc.results, sc.ticket);
   else k_moments<T, false><<<tiles * nbatch, NTHREADS, 0, st>>>(x, g, M, tiles, sc.partials, sc.results, sc.ticket);
   GPE_CUDA(cudaGetLastError());
@@ -237,6 +249,7 @@ template <typename T>
 gpe_status launch_axpby(const void* x, const void* g, const double* coef, int stride_coef, long long M, int nbatch,
                         void* out, int cplx, cudaStream_t st) {
   const long long n = M * nbatch;
+  ProfScope ps(kernel_name("axpby", sizeof(T) == 8, cplx, -1), st);
   if (cplx) k_axpby<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(x, g, coef, stride_coef, M, nbatch, out);
   else k_axpby<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(x, g, coef, stride_coef, M, nbatch, out);
   GPE_CUDA(cudaGetLastError());
@@ -245,14 +258,18 @@ gpe_status launch_axpby(const void* x, const void* g, const double* coef, int st
 
 template <typename T>
 gpe_status launch_inject(const GridHost& gf, const GridHost& gc, const void* f, void* c, cudaStream_t st) {
-  const int off = gf.disc == GPE_FOURIER ? 0 : 1;
+  const int dirichlet = gf.disc == GPE_FOURIER ? 0 : 1;
+  const int r = gf.N[0] / gc.N[0];
+  for (int a = 0; a < gf.dim; ++a)
+    if (gf.N[a] != r * gc.N[a]) return fail(GPE_EINVAL, "injection needs the same refinement on every axis");
   const long long n = gc.M * gc.nbatch;
+  ProfScope ps(kernel_name("inject", sizeof(T) == 8, gf.is_complex, -1), st);
   if (gf.is_complex)
-    k_inject<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(f, c, gf.dim, gf.ext[0], gf.ext[1], gc.ext[0], gc.ext[1],
-                                                         gc.ext[2], off, gf.M, gc.M, gc.nbatch);
+    k_inject<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(f, c, gf.dim, gf.ext[0], gf.ext[1], gc.ext[0], gc.ext[1], r,
+                                                         dirichlet, gf.M, gc.M, gc.nbatch);
   else
-    k_inject<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(f, c, gf.dim, gf.ext[0], gf.ext[1], gc.ext[0], gc.ext[1],
-                                                          gc.ext[2], off, gf.M, gc.M, gc.nbatch);
+    k_inject<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(f, c, gf.dim, gf.ext[0], gf.ext[1], gc.ext[0], gc.ext[1], r,
+                                                          dirichlet, gf.M, gc.M, gc.nbatch);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
 }
@@ -268,6 +285,7 @@ gpe_status launch_prolong(const GridHost& gc, const GridHost& gf, const GridDev<
     oext[a] = gf.ext[a];
     const long long Mc = (long long)ext[0] * ext[1] * ext[2];
     const long long Mf = (long long)oext[0] * oext[1] * oext[2];
+    ProfScope ps(kernel_name("prolong", sizeof(T) == 8, gc.is_complex, -1), st);
     if (gc.disc == GPE_FD) {
       const long long n = Mf * gc.nbatch;
       if (gc.is_complex)

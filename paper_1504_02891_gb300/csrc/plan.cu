@@ -2,6 +2,9 @@
 #include <math.h>
 #include <string.h>
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include "gpe_internal.h"
 
@@ -19,6 +22,67 @@ gpe_status fail(gpe_status st, const std::string& msg) {
 gpe_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? GPE_ENOMEM : GPE_ECUDA;
+}
+
+// ---------------------------------------------------------------- instrumentation
+static std::atomic<long long> g_launches{0};
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+static std::vector<ProfRec> g_recs;
+
+void instr_count(long long n) { g_launches += n; }
+bool prof_enabled() { return g_prof.load(); }
+
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) {
+  st = s;
+  if (capturing(s)) return;   // counted when the graph is launched
+  g_launches += 1;
+  if (!g_prof.load()) return;
+  ProfRec r;
+  r.name = name;
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+  cudaEventRecord(r.a, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  slot = (int)g_recs.size();
+  g_recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_recs.size()) cudaEventRecord(g_recs[slot].b, st);
+}
+
+const char* kernel_name(const char* base, int f64, int cplx, int epi, long long points) {
+  static const char* epis[] = {"acc", "grad", "hess", "F", "W", "ratio"};
+  static std::mutex mu;
+  static std::map<std::string, std::string> names;
+  std::string k = std::string(base) + (f64 ? "_f64" : "_f32") + (cplx ? "_c" : "_r");
+  if (epi >= 0 && epi < 6) k += std::string("_") + epis[epi];
+  if (points >= 0) k += "@" + std::to_string(points);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(k);
+  if (it == names.end()) it = names.emplace(k, k).first;
+  return it->second.c_str();
+}
+
+static void prof_clear() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_recs) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  g_recs.clear();
 }
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -343,6 +407,42 @@ extern "C" gpe_status gpe_prolong(gpe_plan c, gpe_plan f, const void* psi_c, voi
                             : do_prolong<double>(c, f, *c->d64, *f->d64, psi_c, psi_f);
 }
 
+extern "C" int64_t gpe_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+extern "C" gpe_status gpe_profile_enable(int on) {
+  if (!on) prof_clear();
+  g_prof = on != 0;
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_profile_summary(char* buf, int buflen) {
+  if (!buf || buflen <= 0) return fail(GPE_EINVAL, "buffer is NULL");
+  std::map<std::string, std::pair<long long, double>> agg;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_recs) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.b) != cudaSuccess) continue;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+      auto& e = agg[r.name];
+      e.first += 1;
+      e.second += ms;
+    }
+  }
+  std::string out = "{";
+  bool first = true;
+  char tmp[256];
+  for (auto& kv : agg) {
+    snprintf(tmp, sizeof(tmp), "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+             kv.second.second);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  snprintf(buf, buflen, "%s", out.c_str());
+  return GPE_OK;
+}
+
 extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   if (!o) return fail(GPE_EINVAL, "opts is NULL");
   memset(o, 0, sizeof(*o));
@@ -357,7 +457,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->delta_stop = 1e-8;
   o->res_tol = 1e-9;
   o->delta0 = 1.0;
-  o->switch_rel = 2e-6;
+  o->switch_rel = 1e-6;
   o->chunk = 16;
   o->use_graphs = 1;
   return GPE_OK;

@@ -9,6 +9,8 @@
 // graph per level and objective) and reads the small control block between
 // chunks to learn whether the run has stopped.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 #include <chrono>
 #include <memory>
@@ -36,6 +38,7 @@ struct Level {
   Alg1Ctl* h_ctl = nullptr;
   RNCtl* h_rn = nullptr;
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};   // objective F, W
+  size_t chunk_nodes[2] = {0, 0};
   int chunk_len = 0;
 
   gpe_status create(const GridHost& gh) {
@@ -102,6 +105,17 @@ struct Level {
   }
 };
 
+// GPE_TRACE=1 in the environment prints one line per regularized Newton
+// iteration (and per Algorithm 1 run) to stderr.
+static bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("GPE_TRACE");
+    on = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
+
 struct RunStats {
   int iters = 0, nfe = 0, status = 0;
   double F = 0, res = 0, theta = 0;
@@ -134,7 +148,7 @@ static gpe_status queue_iters(Level<T>& L, int objective, int n, cudaStream_t st
 
 template <typename T>
 static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cudaStream_t st) {
-  if (!P.use_graphs) return queue_iters<T>(L, objective, P.chunk, st);
+  if (!P.use_graphs || prof_enabled()) return queue_iters<T>(L, objective, P.chunk, st);
   cudaGraphExec_t& ex = L.chunk_exec[objective];
   if (!ex || L.chunk_len != P.chunk) {
     if (ex) {
@@ -147,12 +161,16 @@ static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cu
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (s != GPE_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    L.chunk_nodes[objective] = nn;
     e = cudaGraphInstantiate(&ex, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     L.chunk_len = P.chunk;
   }
   GPE_CUDA(cudaGraphLaunch(ex, st));
+  instr_count((long long)L.chunk_nodes[objective]);
   return GPE_OK;
 }
 
@@ -160,7 +178,8 @@ static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cu
 // (unit norm).  Returns the state of the control block in L.h_ctl.
 template <typename T>
 static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_iter, double res_tol, double eps0,
-                           double delta, const SolveParams& P, cudaStream_t st, RunStats& out, double res_rel = 0.0) {
+                           double delta, const SolveParams& P, cudaStream_t st, RunStats& out, double res_rel = 0.0,
+                           double theta_hint = 0.0, int stall_iters = 0) {
   Alg1Ctl& c = *L.h_ctl;
   memset(&c, 0, sizeof(c));
   c.alpha = L.g.beta / (2.0 * L.g.hvol);
@@ -183,6 +202,8 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
   c.has_cur = 0;
   c.done = 0;
   c.phase = 0;
+  c.theta_hint = theta_hint;
+  c.stall_iters = stall_iters;
   GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   // first evaluation (no step)
   gpe_status s = apply_op<T>(L.g, L.d, L.solver_data(objective), objective == 1 ? EPI_W : EPI_F, L.acc, false, st);
@@ -205,6 +226,10 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
   out.F = L.h_ctl->F_cur;
   out.res = L.h_ctl->res;
   out.theta = L.h_ctl->theta_c;
+  if (trace_on())
+    fprintf(stderr, "[gpe] alg1 %s M=%lld obj=%d iters=%d nfe=%d status=%d F=%.15g res=%.3e tau=%.3e th=%.10g\n",
+            sizeof(T) == 8 ? "f64" : "f32", L.M, objective, out.iters, out.nfe, out.status, out.F, out.res,
+            L.h_ctl->tau, out.theta);
   if (L.h_ctl->status == GPE_ENONFINITE) return fail(GPE_ENONFINITE, "non-finite energy during Algorithm 1");
   return GPE_OK;
 }
@@ -219,11 +244,11 @@ struct LevelStats {
 // mode_f32: stop on the float32 criteria (relative residual or stagnation).
 template <typename T>
 static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool stop_f32, cudaStream_t st,
-                         LevelStats& ls) {
+                         LevelStats& ls, double theta_start) {
   RunStats r;
   const double res_tol = P.res_tol_X;
   // warm start (Algorithm 1, <= k_init iterations; k_init = 0 is one evaluation)
-  gpe_status s = alg1_run<T>(L, 0, 0, k_init, res_tol, P.eps0, 0.0, P, st, r);
+  gpe_status s = alg1_run<T>(L, 0, 0, k_init, res_tol, P.eps0, 0.0, P, st, r, 0.0, theta_start);
   if (s != GPE_OK) return s;
   ls.inner += r.iters;
   ls.nfe += r.nfe;
@@ -240,7 +265,7 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
     // subproblem (Eq. tr-sub) by Algorithm 1 on W^(k) from X^k
     GPE_CUDA(cudaMemcpyAsync(L.xs[0], L.xk, L.bytes, cudaMemcpyDeviceToDevice, st));
     const double sub_tol = fmax(1e-2 * resk, 1e-14);
-    s = alg1_run<T>(L, 1, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r);
+    s = alg1_run<T>(L, 1, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r, 0.0, thk);
     if (s != GPE_OK) return s;
     ls.inner += r.iters;
     ls.nfe += r.nfe;
@@ -280,11 +305,15 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
     const bool accepted = L.h_rn->accepted != 0;
     const double dmax = L.h_rn->dmax;
     delta = L.h_rn->delta;
+    if (trace_on())
+      fprintf(stderr, "[gpe] rn %s M=%lld outer=%d res=%.3e sub_tol=%.3e inner=%d rho=%.6f ared=%.6e pred=%.6e delta=%.3e dmax=%.3e acc=%d\n",
+              sizeof(T) == 8 ? "f64" : "f32", L.M, outer, resk, sub_tol, r.iters, L.h_rn->rho, L.h_rn->ared,
+              L.h_rn->pred, delta, dmax, (int)accepted);
     if (!isfinite(L.h_rn->rho)) return fail(GPE_ENONFINITE, "non-finite ratio in the regularized Newton step");
     if (accepted) {
       rejects = 0;
       // gradient at the accepted point (Eq. update-X): one evaluation
-      s = alg1_run<T>(L, 0, zc, 0, 0.0, 0.0, 0.0, P, st, r);
+      s = alg1_run<T>(L, 0, zc, 0, 0.0, 0.0, 0.0, P, st, r, 0.0, thk);
       if (s != GPE_OK) return s;
       ls.nfe += r.nfe;
       const int c2 = L.h_ctl->cur;
@@ -298,13 +327,17 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
       ++rejects;
     }
     if (stop_f32) {
-      if (resk < 0.5 * best_res) {
-        best_res = resk;
-        stall = 0;
-      } else if (++stall >= 3) {
-        break;   // float32 stagnation
+      // float32 stagnation: three accepted steps in a row without halving the
+      // best residual, or four rejections in a row
+      if (accepted) {
+        if (resk < 0.5 * best_res) {
+          best_res = resk;
+          stall = 0;
+        } else if (++stall >= 3) {
+          break;
+        }
       }
-      if (rejects >= 3) break;
+      if (rejects >= 4) break;
     }
   }
   ls.F = Fk;
@@ -313,14 +346,16 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
   return GPE_OK;
 }
 
-// Algorithm 1 only (method = 1): result in xk/gk.
+// Algorithm 1 only (method = 1, and the float32 bulk of the mixed schedule):
+// result in xk/gk.  In float32 the run stops at the relative residual
+// switch_rel or when the residual stops improving (the float32 floor).
 template <typename T>
-static gpe_status fg_run(Level<T>& L, const SolveParams& P, bool stop_f32, cudaStream_t st, LevelStats& ls) {
+static gpe_status fg_run(Level<T>& L, const SolveParams& P, bool stop_f32, cudaStream_t st, LevelStats& ls,
+                         double theta_start) {
   RunStats r;
-  // float32: stop on the relative residual instead of Eq. crit1 (the step
-  // size test cannot see below float32 rounding)
   const double eps0 = stop_f32 ? 0.0 : P.eps0;
-  gpe_status s = alg1_run<T>(L, 0, 0, P.max_iter, P.res_tol_X, eps0, 0.0, P, st, r, stop_f32 ? P.switch_rel : 0.0);
+  gpe_status s = alg1_run<T>(L, 0, 0, P.max_iter, P.res_tol_X, eps0, 0.0, P, st, r, stop_f32 ? P.switch_rel : 0.0,
+                             theta_start, stop_f32 ? 40 : 0);
   if (s != GPE_OK) return s;
   const int cur = L.h_ctl->cur;
   GPE_CUDA(cudaMemcpyAsync(L.xk, L.xs[cur], L.bytes, cudaMemcpyDeviceToDevice, st));
@@ -412,14 +447,19 @@ static gpe_status prolong_into(Level<T>& Lc, Level<T>& Lf, cudaStream_t st) {
 template <typename T>
 static gpe_status solve_levels(std::vector<std::unique_ptr<Level<T>>>& lv, const SolveParams& P, bool f32,
                                cudaStream_t st, LevelStats& fine_stats, int& nfe_total) {
+  double theta = 0.0;   // theta of the previous level: a nearby value for the first evaluation
   for (size_t l = 0; l < lv.size(); ++l) {
     if (l > 0) {
       gpe_status s = prolong_into<T>(*lv[l - 1], *lv[l], st);
       if (s != GPE_OK) return s;
     }
     LevelStats ls;
-    gpe_status s = P.method == 1 ? fg_run<T>(*lv[l], P, f32, st, ls) : rn_run<T>(*lv[l], P, P.k_init, f32, st, ls);
+    // float32 bulk of the mixed schedule: Algorithm 1 down to the float32
+    // floor on every level (the regularized Newton steps run in float64)
+    gpe_status s = (P.method == 1 || f32) ? fg_run<T>(*lv[l], P, f32, st, ls, theta)
+                                          : rn_run<T>(*lv[l], P, P.k_init, f32, st, ls, theta);
     if (s != GPE_OK) return s;
+    theta = ls.theta;
     nfe_total += ls.nfe;
     if (l + 1 == lv.size()) fine_stats = ls;
   }
@@ -515,13 +555,13 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
     LevelStats ls;
     if (o.mode == 1) {
       SolveParams P64 = P;
-      s = rn_run<double>(*fin, P64, 0, false, st, ls);
+      s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta);
       rep.outer_f64 = ls.outer;
       rep.inner_f64 = ls.inner;
     } else {
       SolveParams P64 = P;
       P64.max_outer = 0;
-      s = rn_run<double>(*fin, P64, 0, false, st, ls);
+      s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta);
     }
     if (s != GPE_OK) return s;
     nfe += ls.nfe;
