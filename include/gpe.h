@@ -181,6 +181,30 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
 gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
                              gpe_solve_report* report);
 
+/* Allocation-free Cayley step (the paper has no counterpart: this is a
+ * packaging variant of gpe_feasible_step for callers that cannot call
+ * cudaMalloc -- e.g. code running inside a stream capture that must stay free
+ * of allocation calls, inside an allocator or memory-pool callback, or under a
+ * fixed up-front memory budget -- and so cannot create a plan).
+ * Computes the same result as gpe_feasible_step(..., E_out = NULL) for
+ * `nbatch` instances of `n_unknowns` values each: psi and hpsi are device
+ * buffers in the layout above (prec = gpe_prec, is_complex as in the problem),
+ * h_vol the cell volume, tau >= 0.  psi_out (device, same layout) must not
+ * alias psi or hpsi.  stream is a cudaStream_t (NULL = legacy default stream);
+ * the call is asynchronous.
+ * Scratch: a fixed 512 KiB array in device memory, part of the library image,
+ * held by every GPU that loads the library until the process exits.  Limits:
+ * 1 <= nbatch <= 64 and nbatch * min(ceil(n_unknowns / 256), 512) <= 4096;
+ * larger requests return GPE_EINVAL and do nothing.
+ * The first call on each device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race;
+ * serialise them.  The call allocates nothing. */
+gpe_status gpe_feasible_step_noalloc(int prec, int is_complex, int64_t n_unknowns, int nbatch, double h_vol,
+                                     const void* psi, const void* hpsi, double tau, void* psi_out,
+                                     void* stream);
+
 /* Instrumentation (the paper has no counterpart; used by the benchmark).
  * gpe_kernel_launches: kernels this process has launched through libgpe so far
  *   (a CUDA-graph launch counts each of its kernel nodes).
