@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--only", choices=["happly", "solve"], default=None,
+                    help="profiling aid: run only the H-apply loop (3 warm-up + 10 applies) or only two "
+                         "mixed solves of the workload, print a one-line summary, no JSON contract line")
     return ap.parse_args()
 
 
@@ -376,8 +379,46 @@ def our_arm(args):
         dist.destroy_process_group()
 
 
+def profiling_run(args):
+    """Small fixed runs for ncu captures (see profiles/)."""
+    import torch
+    import workloads as W
+    import paper_1504_02891_gb300 as G
+    G.load()
+    if args.only == "happly":
+        p = W.config("c4")
+        plan = G.Plan(p, nbatch=64, prec=G.F32)
+        psi = plan.empty()
+        psi.real.normal_()
+        psi.imag.normal_()
+        psi.mul_(1e-2)
+        out = plan.empty()
+        for _ in range(3):
+            plan.grad(psi, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            plan.grad(psi, out)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"happly us/apply {e0.elapsed_time(e1) / 10 * 1e3:.1f}")
+    else:
+        p = W.config("c2")
+        plan = G.Plan(p)
+        init = G.to_device(W.gaussian(p))
+        for _ in range(2):
+            t = init.clone()
+            rep = plan.solve(t, mode=1, levels=3, res_tol=RES_TOL)
+        torch.cuda.synchronize()
+        print("solve", rep)
+
+
 def main():
     args = parse()
+    if args.only:
+        profiling_run(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

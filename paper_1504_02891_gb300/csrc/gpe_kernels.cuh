@@ -87,6 +87,7 @@ struct PassGeom {
   long long stride;     // element stride along the axis
   long long ostride;    // axes 1,2: stride of the outer index
   int F, logF;          // FFT length
+  int P;                // row pitch of the shared-memory FFT buffers (padded, see pidx)
   int odd_ext;          // sine grid: odd extension to 2N
   int LB;               // data lines per tile (power of two, <= MAXLB)
   int logLB;
@@ -98,6 +99,7 @@ struct PassGeom {
   const typename C2t<T>::type* tw;  // e^{-2 pi i k / F}
   const T* lam;         // wavenumber of FFT index m
   T c2, c1;             // symbol = c2*lam^2 + c1*coord*lam  (1/F folded in)
+  T dlam;               // lam of FFT index m = dlam * p(m), p(m) = m or m - F
   const T* rcoord;      // rotation coordinate table (x or y nodes) or null
 };
 

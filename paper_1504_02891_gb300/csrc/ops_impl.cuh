@@ -43,6 +43,42 @@ template <typename C> __device__ __forceinline__ C mk(double re, double im);
 template <> __device__ __forceinline__ float2 mk<float2>(double re, double im) { return make_float2((float)re, (float)im); }
 template <> __device__ __forceinline__ double2 mk<double2>(double re, double im) { return make_double2(re, im); }
 
+// ----------------------------------------------------------------- accumulators
+// Per-thread sums of the float64 reductions.  In float32 kernels they are kept
+// as unevaluated float pairs (hi + lo, Knuth two-sum), so no float64 unit is
+// touched per element (GB300's float64 rate is a small fraction of float32);
+// the pairs become float64 once per warp.  Float64 kernels accumulate in
+// double.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void acc_zero(DF& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void acc_add(DF& a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b - bb);
+  a.hi = s;
+  a.lo += err;
+}
+__device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ void acc_merge(DF& a, const DF& b) {
+  acc_add(a, b.hi);
+  a.lo += b.lo;
+}
+__device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
+__device__ __forceinline__ double acc_value(const DF& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ DF shfl_down(const DF& a, int o) {
+  DF r;
+  r.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+  r.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+  return r;
+}
+__device__ __forceinline__ double shfl_down(double a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+template <typename T> struct AccT { using type = double; };
+template <> struct AccT<float> { using type = DF; };
+
 // ----------------------------------------------------------------- tile geometry
 // Base offset of data line l of a tile; false if the line lies outside the grid.
 // ri receives the index into the rotation coordinate table.
@@ -70,7 +106,8 @@ __device__ __forceinline__ bool line_base(const PassGeom<T>& G, int inst, int ti
 // contiguously in `a`; `b` is scratch of the same size.  Returns the buffer that
 // holds the result.  Ends with a barrier.
 template <typename C>
-__device__ C* fft_lines(C* a, C* b, int F, int nl, const C* __restrict__ tw) {
+__device__ C* fft_lines(C* a, C* b, int F, int nl, const C* __restrict__ tw, int P = 0) {
+  if (P == 0) P = F;     // row pitch (>= F; padded rows avoid bank conflicts)
   C* src = a;
   C* dst = b;
   for (int Ns = 1; Ns < F;) {
@@ -82,8 +119,8 @@ __device__ C* fft_lines(C* a, C* b, int F, int nl, const C* __restrict__ tw) {
       const int line = t / nb;
       const int j = t - line * nb;
       const int k = j & (Ns - 1);
-      const C* s = src + line * F + j;
-      C* d = dst + line * F + (j - k) * R + k;
+      const C* s = src + line * P + j;
+      C* d = dst + line * P + (j - k) * R + k;
       if (R == 4) {
         C v0 = s[0], v1 = s[nb], v2 = s[2 * nb], v3 = s[3 * nb];
         if (Ns > 1) {
@@ -111,25 +148,212 @@ __device__ C* fft_lines(C* a, C* b, int F, int nl, const C* __restrict__ tw) {
   return src;
 }
 
+// ----------------------------------------------------------------- register-radix FFT
+// Mixed-radix Stockham FFT (radix 16/8/4/2 butterflies in registers, 2-3
+// shared-memory stages for F <= 1024) on nl lines of length F with row pitch P
+// and padded indexing pidx(i) = i + i/16 (one spare slot every 16 elements),
+// which keeps the stride-16 scatter of the first stage free of bank conflicts.
+// Forward sign, unnormalised.  `post(line, m, v)` is applied to every output of
+// the last stage (m = frequency index), e.g. the spectral symbol.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+template <typename C> __device__ __forceinline__ C cmulc(C v, double wr, double wi) {
+  using T = decltype(v.x);
+  C r;
+  r.x = v.x * (T)wr - v.y * (T)wi;
+  r.y = v.x * (T)wi + v.y * (T)wr;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C mul_mi(C v) {   // -i v
+  C r;
+  r.x = v.y;
+  r.y = -v.x;
+  return r;
+}
+
+template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  const C t = a;
+  a = t + b;
+  b = t - b;
+}
+template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C s02 = v0 + v2, d02 = v0 - v2, s13 = v1 + v3, d13 = v1 - v3;
+  v0 = s02 + s13;
+  v2 = s02 - s13;
+  v1 = d02 + mul_mi(d13);
+  v3 = d02 - mul_mi(d13);
+}
+// cos(pi/8), sin(pi/8), sqrt(2)/2
+#define GPE_C8 0.92387953251128675613
+#define GPE_S8 0.38268343236508977173
+#define GPE_R2 0.70710678118654752440
+template <typename C> __device__ __forceinline__ void dft8(C* v) {
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  o1 = cmulc(o1, GPE_R2, -GPE_R2);
+  o2 = mul_mi(o2);
+  o3 = cmulc(o3, -GPE_R2, -GPE_R2);
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+template <typename C> __device__ __forceinline__ void dft16(C* v) {
+  C e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft8(e);
+  dft8(o);
+  o[1] = cmulc(o[1], GPE_C8, -GPE_S8);
+  o[2] = cmulc(o[2], GPE_R2, -GPE_R2);
+  o[3] = cmulc(o[3], GPE_S8, -GPE_C8);
+  o[4] = mul_mi(o[4]);
+  o[5] = cmulc(o[5], -GPE_S8, -GPE_C8);
+  o[6] = cmulc(o[6], -GPE_R2, -GPE_R2);
+  o[7] = cmulc(o[7], -GPE_C8, -GPE_S8);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[i] = e[i] + o[i];
+    v[i + 8] = e[i] - o[i];
+  }
+}
+template <typename C, int R> __device__ __forceinline__ void dft_r(C* v) {
+  if constexpr (R == 2) dft2(v[0], v[1]);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8(v);
+  else dft16(v);
+}
+
+// One Stockham stage of radix R = 2^LR.
+template <typename C, int LR, typename Post>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restrict__ dst, int logF, int logNs, int nl,
+                                          int P, const C* __restrict__ tw, bool last, Post& post) {
+  constexpr int R = 1 << LR;
+  const int lognb = logF - LR;
+  const int nb = 1 << lognb;
+  const int Ns = 1 << logNs;
+  const int tot = nl << lognb;
+  const int logtw = logF - logNs - LR;        // twiddle step F / (Ns R)
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int line = t >> lognb;
+    const int j = t & (nb - 1);
+    const int k = j & (Ns - 1);
+    const C* s = src + line * P;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[pidx(j + (r << lognb))];
+    if (Ns > 1) {
+      // twiddles w^r, w = e^{-2 pi i k / (Ns R)}, from w, w^2, w^4, w^8 of the table
+      const int e = k << logtw;
+      C w[R];
+      w[1] = tw[e];
+      if constexpr (R >= 4) {
+        w[2] = tw[2 * e];
+        w[3] = cmul(w[1], w[2]);
+      }
+      if constexpr (R >= 8) {
+        w[4] = tw[4 * e];
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+      }
+      if constexpr (R >= 16) {
+        w[8] = tw[8 * e];
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+    }
+    dft_r<C, R>(v);
+    C* d = dst + line * P;
+    const int mb = ((j - k) << LR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = mb + (r << logNs);
+      d[pidx(m)] = last ? post(line, m, v[r]) : v[r];
+    }
+  }
+}
+
+struct PostNone {
+  template <typename C> __device__ __forceinline__ C operator()(int, int, C v) const { return v; }
+};
+
+// Radix schedule: ceil(logF/4) stages with the bits spread evenly (16x16 for
+// 256, 8x8x8 for 512, 16x8x8 for 1024, ...).  Ends with a barrier.
+template <typename C, typename Post>
+__device__ C* fft_run(C* a, C* b, int logF, int nl, int P, const C* tw, Post post) {
+  const int S = (logF + 3) >> 2;
+  const int base = S ? logF / S : 0, extra = S ? logF % S : 0;
+  C* src = a;
+  C* dst = b;
+  int logNs = 0;
+  for (int st = 0; st < S; ++st) {
+    const int lr = base + (st < extra ? 1 : 0);
+    const bool last = st == S - 1;
+    switch (lr) {
+      case 1: fft_stage<C, 1>(src, dst, logF, logNs, nl, P, tw, last, post); break;
+      case 2: fft_stage<C, 2>(src, dst, logF, logNs, nl, P, tw, last, post); break;
+      case 3: fft_stage<C, 3>(src, dst, logF, logNs, nl, P, tw, last, post); break;
+      default: fft_stage<C, 4>(src, dst, logF, logNs, nl, P, tw, last, post); break;
+    }
+    __syncthreads();
+    C* t = src;
+    src = dst;
+    dst = t;
+    logNs += lr;
+  }
+  return src;
+}
+
+// Asynchronous global -> shared copies (cp.async, sm_80+): the whole tile is in
+// flight at once instead of one dependent load per thread and iteration.
+template <typename V>
+__device__ __forceinline__ void cp_async(V* dst_smem, const V* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(V) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+  } else if constexpr (sizeof(V) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ----------------------------------------------------------------- block reductions
-// Reduce acc[0..NQ) over the block (slot Q_MAX is a max), write this CTA's
-// partials, and let the last CTA fold all partials per instance in a fixed order
-// into results[inst][q].  Returns true in the last CTA (all threads).
-static __device__ bool reduce_partials(double (&acc)[NQ], int nq, double* partials, double* results,
-                                unsigned int* ticket, int tiles_per_inst) {
+// Reduce the per-thread sums acc[0..nq) and the max slot acc_max over the
+// block, write this CTA's float64 partials, and let the last CTA fold all
+// partials per instance in a fixed order into results[inst][q] (deterministic).
+// Slots >= nq (other than Q_MAX) are written as 0.  Returns true in the last
+// CTA (all threads).
+template <typename A>
+static __device__ bool reduce_partials(A (&acc)[NQ], double acc_max, int nq, double* partials, double* results,
+                                       unsigned int* ticket, int tiles_per_inst) {
   __shared__ double red[NTHREADS / 32][NQ];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  (void)nq;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double v = acc[q];
-    for (int o = 16; o > 0; o >>= 1) {
-      double w = __shfl_down_sync(0xffffffffu, v, o);
-      v = (q == Q_MAX) ? fmax(v, w) : v + w;
+    if (q == Q_MAX) {
+      double v = acc_max;
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+      if (lane == 0) red[warp][q] = v;
+    } else if (q < nq) {
+      A v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) acc_merge(v, shfl_down(v, o));
+      if (lane == 0) red[warp][q] = acc_value(v);
+    } else if (lane == 0) {
+      red[warp][q] = 0.0;
     }
-    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
   if (threadIdx.x < NQ) {
@@ -153,15 +377,20 @@ static __device__ bool reduce_partials(double (&acc)[NQ], int nq, double* partia
       const double* p = partials + ((size_t)b * tiles_per_inst + i) * NQ;
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        double w = __ldcg(p + q);
+        if (q >= nq && q != Q_MAX) continue;
+        const double w = __ldcg(p + q);
         v[q] = (q == Q_MAX) ? fmax(v[q], w) : v[q] + w;
       }
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
+      if (q >= nq && q != Q_MAX) {
+        if (lane == 0) red[warp][q] = 0.0;
+        continue;
+      }
       double x = v[q];
       for (int o = 16; o > 0; o >>= 1) {
-        double w = __shfl_down_sync(0xffffffffu, x, o);
+        const double w = __shfl_down_sync(0xffffffffu, x, o);
         x = (q == Q_MAX) ? fmax(x, w) : x + w;
       }
       if (lane == 0) red[warp][q] = x;
@@ -321,18 +550,17 @@ struct EpiCtx {
   T nl, shift, lin_scale, th_c, delta;
 };
 
-template <typename T, bool CPLX, int EPI>
+template <typename T, bool CPLX, int EPI, typename A>
 __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long long gi,
                                                typename VT<T, CPLX>::V x,
-                                               typename VT<T, CPLX>::V lin, double (&acc)[NQ]) {
+                                               typename VT<T, CPLX>::V lin, A (&acc)[NQ], double& amax) {
   using V = typename VT<T, CPLX>::V;
   if (EPI == EPI_GRAD) {
     const T x2 = tre(x, x);
     if (E.out) E.out[gi] = lin + (E.nl * x2) * x;
-    const double dx2 = dre(x, x);
-    acc[0] += dre(x, lin);
-    acc[1] += dx2 * dx2;
-    acc[2] += dx2;
+    acc_add(acc[0], tre(x, lin));
+    acc_add(acc[1], x2 * x2);
+    acc_add(acc[2], x2);
   } else if (EPI == EPI_HESS) {
     const V p = E.base[gi];
     const T p2 = tre(p, p);
@@ -349,31 +577,30 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
       const T x2 = tre(xk, xk);
       const T R = tre(xk, dd);
       g = E.lin_scale * lin + (T(4) * E.nl * x2) * y + (T(8) * E.nl * R) * xk + E.delta * dd;
-      const double dx2 = (double)x2, dR = dre(xk, dd), dd2 = dre(dd, dd);
-      acc[Q_WX] += 4.0 * (double)E.nl * dx2 * dR + 2.0 * (double)E.nl * (dx2 * dd2 + 2.0 * dR * dR)
-                   + 0.5 * (double)E.delta * dd2;
+      const T d2 = tre(dd, dd);
+      acc_add(acc[Q_WX], T(4) * E.nl * x2 * R + T(2) * E.nl * (x2 * d2 + T(2) * R * R) + T(0.5) * E.delta * d2);
     }
     E.out[gi] = g;
-    const double y2 = dre(y, y);
-    acc[Q_E2] += dre(y, lin);
-    acc[Q_E4] += y2 * y2;
-    acc[Q_NY] += y2;
-    acc[Q_YG] += dre(y, g);
-    acc[Q_GG] += dre(g, g);
+    const T y2 = tre(y, y);
+    acc_add(acc[Q_E2], tre(y, lin));
+    acc_add(acc[Q_E4], y2 * y2);
+    acc_add(acc[Q_NY], y2);
+    acc_add(acc[Q_YG], tre(y, g));
+    acc_add(acc[Q_GG], tre(g, g));
     const V q = g - E.th_c * y;
-    acc[Q_Q] += dre(q, q);
-    acc[Q_QY] += dre(q, y);
+    acc_add(acc[Q_Q], tre(q, q));
+    acc_add(acc[Q_QY], tre(q, y));
     const V xc = E.xc ? E.xc[gi] : vzero<V>();
     const V gc = E.gc ? E.gc[gi] : vzero<V>();
     const V s = y - xc;
     const V v = (g - gc) - E.th_c * s;
-    const double s2 = dre(s, s);
-    acc[Q_SS] += s2;
-    acc[Q_SV] += dre(s, v);
-    acc[Q_VV] += dre(v, v);
-    acc[Q_VY] += dre(v, y);
-    acc[Q_SY] += dre(s, y);
-    acc[Q_MAX] = fmax(acc[Q_MAX], sqrt(s2));
+    const T s2 = tre(s, s);
+    acc_add(acc[Q_SS], s2);
+    acc_add(acc[Q_SV], tre(s, v));
+    acc_add(acc[Q_VV], tre(v, v));
+    acc_add(acc[Q_VY], tre(v, y));
+    acc_add(acc[Q_SY], tre(s, y));
+    amax = fmax(amax, (double)sqrt(s2));
   } else if (EPI == EPI_RATIO) {
     const V d = x;
     const V xk = E.base[gi];
@@ -381,15 +608,15 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     const T x2 = tre(xk, xk);
     const V ax = gk - (T(4) * E.nl * x2) * xk;
     const V z = xk + d;
-    const double dx2 = (double)x2, dR = dre(xk, d), dd2 = dre(d, d);
-    acc[R_AXD] += dre(ax, d);
-    acc[R_DAD] += 2.0 * dre(d, lin);
-    acc[R_QD] += (2.0 * dR + dd2) * (dre(z, z) + dx2);
-    acc[R_X2D2] += dx2 * dd2;
-    acc[R_R2] += dR * dR;
-    acc[R_DD] += dd2;
-    acc[R_GD] += dre(gk, d);
-    acc[Q_MAX] = fmax(acc[Q_MAX], sqrt(dd2));
+    const T R = tre(xk, d), d2 = tre(d, d);
+    acc_add(acc[R_AXD], tre(ax, d));
+    acc_add(acc[R_DAD], T(2) * tre(d, lin));
+    acc_add(acc[R_QD], (T(2) * R + d2) * (tre(z, z) + x2));
+    acc_add(acc[R_X2D2], x2 * d2);
+    acc_add(acc[R_R2], R * R);
+    acc_add(acc[R_DD], d2);
+    acc_add(acc[R_GD], tre(gk, d));
+    amax = fmax(amax, (double)sqrt(d2));
   }
 }
 
@@ -467,30 +694,35 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_off[MAXLB];
   __shared__ T s_rc[MAXLB];
-  C* buf0 = reinterpret_cast<C*>(smem_raw);
-  C* buf1 = buf0 + G.LC * G.F;
+  const int F = G.F, Pt = G.P;
+  const int nt = blockDim.x, tid = threadIdx.x;
   const int inst = blockIdx.x / G.tiles;
   const int tile = blockIdx.x - inst * G.tiles;
-  const int F = G.F;
-  const int nt = blockDim.x, tid = threadIdx.x;
 
+  // operands: src0 (input, or X_cur for the Cayley step), src1 (x_sub or G_cur), acc_in
   const V* xin = (const V*)D.x;
   V* yst = nullptr;
-  const V* xcur = nullptr;
-  const V* gcur = nullptr;
+  const V* src1 = (const V*)D.xsub;
   T sa = 0, sb = 0;
   if (D.use_slots) {
     const Alg1Ctl* c = D.ctl;
     xin = (const V*)D.xs[c->trial];
     if (D.step_on_load) {
       yst = (V*)D.xs[c->trial];
-      xcur = (const V*)D.xs[c->cur];
-      gcur = (const V*)D.gs[c->cur];
+      xin = (const V*)D.xs[c->cur];
+      src1 = (const V*)D.gs[c->cur];
       sa = (T)(c->s * c->a);
       sb = (T)(c->s * c->b);
     }
   }
-  const V* xsub = (const V*)D.xsub;
+  const V* accin = (const V*)D.acc_in;
+  const int tile_n = G.LB * G.len;
+  C* tw_s = reinterpret_cast<C*>(smem_raw);
+  C* buf0 = tw_s + F;
+  C* buf1 = buf0 + G.LC * Pt;
+  V* st0 = reinterpret_cast<V*>(buf1 + G.LC * Pt);
+  V* st1 = st0 + tile_n;
+  V* st2 = st1 + (src1 ? tile_n : 0);
 
   for (int l = tid; l < G.LB; l += nt) {
     long long b;
@@ -499,84 +731,88 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
     s_off[l] = ok ? b : -1;
     if (G.rcoord) s_rc[l] = G.rcoord[ok ? ri : 0];
   }
-  for (int i = tid; i < G.LC * F; i += nt) buf0[i] = mk<C>(0.0, 0.0);
+  for (int i = tid; i < F; i += nt) cp_async(tw_s + i, G.tw + i);
+  __syncthreads();
+  // the whole tile (and the operands the epilogue needs) in flight at once
+  visit_tile(G, s_off, [&](int l, int j, long long gi) {
+    const int q = G.axis == 0 ? l * G.len + j : j * G.LB + l;
+    cp_async(st0 + q, xin + gi);
+    if (src1) cp_async(st1 + q, src1 + gi);
+    if (accin) cp_async(st2 + q, accin + gi);
+  });
+  for (int i = tid; i < G.LC * Pt; i += nt) buf0[i] = mk<C>(0.0, 0.0);
+  cp_async_wait_all();
   __syncthreads();
 
   visit_tile(G, s_off, [&](int l, int j, long long gi) {
-    V v;
-    if (yst) {
-      v = sa * xcur[gi] + sb * gcur[gi];
-      yst[gi] = v;
-    } else {
-      v = xin[gi];
-      if (xsub) v = v - xsub[gi];
+    const int q = G.axis == 0 ? l * G.len + j : j * G.LB + l;
+    V v = st0[q];
+    if (src1) {
+      v = yst ? sa * v + sb * st1[q] : v - st1[q];
+      st0[q] = v;
+      if (yst) yst[gi] = v;
     }
     const int m = G.odd_ext ? j + 1 : j;
     if constexpr (CPLX) {
-      C* row = buf0 + l * F;
-      row[m] = v;
-      if (G.odd_ext) row[F - m] = -v;
+      C* row = buf0 + l * Pt;
+      row[pidx(m)] = v;
+      if (G.odd_ext) row[pidx(F - m)] = -v;
     } else {
-      T* row = reinterpret_cast<T*>(buf0 + (l >> 1) * F);
+      T* row = reinterpret_cast<T*>(buf0 + (l >> 1) * Pt);
       const int comp = l & 1;
-      row[2 * m + comp] = v;
-      if (G.odd_ext) row[2 * (F - m) + comp] = -v;
+      row[2 * pidx(m) + comp] = v;
+      if (G.odd_ext) row[2 * pidx(F - m) + comp] = -v;
     }
   });
   __syncthreads();
 
-  C* r = fft_lines<C>(buf0, buf1, F, G.LC, G.tw);
-  // symbol multiply; the conjugation turns the next forward FFT into the inverse
-  for (int t = tid; t < G.LC * F; t += nt) {
-    const int c = t >> G.logF;
-    const int m = t & (F - 1);
-    const T lm = G.lam[m];
-    T sym = G.c2 * lm * lm;
-    if (G.rcoord) sym += G.c1 * s_rc[c] * lm;
-    C v = r[t];
-    v.x = sym * v.x;
-    v.y = -sym * v.y;
-    r[t] = v;
-  }
-  __syncthreads();
-  C* o = fft_lines<C>(r, r == buf0 ? buf1 : buf0, F, G.LC, G.tw);
+  // forward FFT with the line symbol (and the conjugation that turns the
+  // next forward FFT into the inverse) fused into its last stage
+  const T c2 = G.c2, c1 = G.c1, dlam = G.dlam;
+  const bool rot = G.rcoord != nullptr;
+  auto symbol = [&](int line, int m, C v) -> C {
+    const T lm = dlam * (T)(m < (F >> 1) ? m : m - F);
+    T sym = c2 * lm * lm;
+    if (rot) sym += c1 * s_rc[line] * lm;
+    C r;
+    r.x = sym * v.x;
+    r.y = -sym * v.y;
+    return r;
+  };
+  C* r = fft_run<C>(buf0, buf1, G.logF, G.LC, Pt, tw_s, symbol);
+  C* o = fft_run<C>(r, r == buf0 ? buf1 : buf0, G.logF, G.LC, Pt, tw_s, PostNone());
 
   EpiCtx<T, CPLX> E;
   if (EPI != EPI_ACC) make_ctx<T, CPLX, EPI>(E, D);
-  double acc[NQ];
+  using A = typename AccT<T>::type;
+  A acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-  const V* accin = (const V*)D.acc_in;
+  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+  double amax = 0.0;
   const long long ibase = inst * G.M;
   visit_tile(G, s_off, [&](int l, int j, long long gi) {
+    const int q = G.axis == 0 ? l * G.len + j : j * G.LB + l;
     const int m = G.odd_ext ? j + 1 : j;
     V kin;
     if constexpr (CPLX) {
-      const C ov = o[l * F + m];
+      const C ov = o[l * Pt + pidx(m)];
       kin.x = ov.x;
       kin.y = -ov.y;
     } else {
-      const C ov = o[(l >> 1) * F + m];
+      const C ov = o[(l >> 1) * Pt + pidx(m)];
       kin = (l & 1) ? -ov.y : ov.x;
     }
+    if (accin) kin = kin + st2[q];
     if (EPI == EPI_ACC) {
-      V a = kin;
-      if (accin) a = accin[gi] + a;
-      ((V*)D.out)[gi] = a;
+      ((V*)D.out)[gi] = kin;
       return;
     }
-    V x;
-    if (yst) x = yst[gi];
-    else {
-      x = xin[gi];
-      if (xsub) x = x - xsub[gi];
-    }
-    V lin = kin + D.V[gi - ibase] * x;
-    if (accin) lin = lin + accin[gi];
-    epilogue_point<T, CPLX, EPI>(E, gi, x, lin, acc);
+    const V x = st0[q];
+    const V lin = kin + D.V[gi - ibase] * x;
+    epilogue_point<T, CPLX, EPI>(E, gi, x, lin, acc, amax);
   });
   if (EPI == EPI_ACC || EPI == EPI_HESS || D.nq == 0) return;
-  if (reduce_partials(acc, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
+  if (reduce_partials(acc, amax, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
 }
 
 // ----------------------------------------------------------------- finite differences
@@ -594,9 +830,11 @@ __global__ void __launch_bounds__(NTHREADS) k_fd(FDGeom G, const T* __restrict__
   const V* xsub = (const V*)D.xsub;
   EpiCtx<T, CPLX> E;
   make_ctx<T, CPLX, EPI>(E, D);
-  double acc[NQ];
+  using A = typename AccT<T>::type;
+  A acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+  double amax = 0.0;
   const long long base = inst * G.M;
   const T a0 = (T)G.ih2[0], a1 = (T)G.ih2[1], a2 = (T)G.ih2[2];
   for (long long li = (long long)tb * blockDim.x + threadIdx.x; li < G.M; li += (long long)G.tiles * blockDim.x) {
@@ -640,10 +878,10 @@ __global__ void __launch_bounds__(NTHREADS) k_fd(FDGeom G, const T* __restrict__
       }
     }
     lin = lin + D.V[li] * x;
-    epilogue_point<T, CPLX, EPI>(E, base + li, x, lin, acc);
+    epilogue_point<T, CPLX, EPI>(E, base + li, x, lin, acc, amax);
   }
   if (EPI == EPI_HESS || D.nq == 0) return;
-  if (reduce_partials(acc, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
+  if (reduce_partials(acc, amax, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
 }
 
 // ----------------------------------------------------------------- elementwise kernels
@@ -670,20 +908,21 @@ __global__ void __launch_bounds__(NTHREADS) k_moments(const void* xv, const void
   const V* g = (const V*)gv;
   const int inst = blockIdx.x / tiles;
   const int tb = blockIdx.x - inst * tiles;
-  double acc[NQ];
+  using A = typename AccT<T>::type;
+  A acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
   const long long base = inst * M;
   for (long long i = (long long)tb * blockDim.x + threadIdx.x; i < M; i += (long long)tiles * blockDim.x) {
     const V xi = x[base + i];
-    acc[0] += dre(xi, xi);
+    acc_add(acc[0], tre(xi, xi));
     if (g) {
       const V gi = g[base + i];
-      acc[1] += dre(xi, gi);
-      acc[2] += dre(gi, gi);
+      acc_add(acc[1], tre(xi, gi));
+      acc_add(acc[2], tre(gi, gi));
     }
   }
-  reduce_partials(acc, 3, partials, results, ticket, tiles);
+  reduce_partials(acc, 0.0, 3, partials, results, ticket, tiles);
 }
 
 // out_b = ca[b] * x_b + cb[b] * g_b  (g may be null)

@@ -43,9 +43,13 @@ static PassGeom<T> make_geom(int axis, const int ext[3], int F, int Fbuf, int od
   G.F = F;
   G.logF = ilog2(F);
   G.odd_ext = odd_ext;
-  const int budget = sizeof(T) == 4 ? 4096 : 2048;   // complex elements per buffer
+  // shared memory per complex line: two padded FFT rows + two staged operand
+  // rows (input and accumulator); budget ~96 KiB per CTA
+  const size_t vsz = sizeof(T) * (cplx ? 2 : 1);
+  const size_t per_cline = 2 * (size_t)(Fbuf + Fbuf / 16 + 1) * sizeof(C) + 2 * (size_t)(cplx ? 1 : 2) * ext[axis] * vsz;
+  const size_t budget = 96 * 1024 - (size_t)Fbuf * sizeof(C);
   const int lc_cap = cplx ? MAXLB : MAXLB / 2;
-  const int lc_max = std::max(1, std::min(budget / Fbuf, lc_cap));
+  const int lc_max = std::max(1, std::min((int)(budget / per_cline), lc_cap));
   long long lines = axis == 0 ? (long long)ext[1] * ext[2] : (long long)ext[0] * (axis == 1 ? ext[2] : ext[1]);
   long long tot = lines * nbatch;
   long long tot_c = cplx ? tot : (tot + 1) / 2;
@@ -54,10 +58,10 @@ static PassGeom<T> make_geom(int axis, const int ext[3], int F, int Fbuf, int od
   int lc = pow2floor(std::min<long long>(want, lc_max));
   if (axis != 0) {
     const int x2 = pow2ceil(ext[0]);
-    // strided lines: read rows of >= 8 consecutive values when there is work for the whole GPU
-    const int want_lb = std::min(8, x2);
+    // strided lines: read rows of >= 32 bytes when there is work for the whole GPU
+    const int want_lb = std::min((int)std::max<size_t>(1, 32 / vsz), x2);
     const int want_lc = cplx ? want_lb : std::max(1, want_lb / 2);
-    if (tot_c >= (long long)want_lc * TARGET_CTAS) lc = std::max(lc, std::min(want_lc, lc_max));
+    if (tot_c >= (long long)want_lc * TARGET_CTAS) lc = std::max(lc, std::min(want_lc, pow2floor(lc_max)));
     lc = std::min(lc, cplx ? x2 : std::max(1, x2 / 2));
   }
   G.LC = lc;
@@ -74,7 +78,9 @@ static PassGeom<T> make_geom(int axis, const int ext[3], int F, int Fbuf, int od
   G.nthreads = std::min(NTHREADS, std::max(64, pow2ceil(std::min(work, NTHREADS))));
   G.tpl = std::min(pow2ceil(G.len), G.nthreads);
   G.ltpl = ilog2(G.tpl);
+  G.P = Fbuf + Fbuf / 16 + 1;   // padded rows (pidx) + 1 to stagger consecutive rows
   *blocks = G.tiles * nbatch;
+  // FFT part only; launch_pass adds the twiddle table and staged operands
   *smem = 2 * (size_t)G.LC * Fbuf * sizeof(C);
   return G;
 }
@@ -114,6 +120,7 @@ gpe_status GridDev<T>::create(const GridHost& g) {
       PassGeom<T> G = make_geom<T>(a, g.ext, F, F, g.disc == GPE_SINE, g.is_complex, g.nbatch, &blocks[a], &smem[a]);
       G.tw = tw[a];
       G.lam = lam[a];
+      G.dlam = (T)(2.0 * M_PI / L);
       G.c2 = (T)(0.5 / F);
       G.c1 = (T)0;
       G.rcoord = nullptr;
@@ -164,7 +171,12 @@ static void allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, bool CPLX, int EPI>
-static gpe_status launch_pass_t(const PassGeom<T>& G, int blocks, size_t smem, const PassData<T>& D, cudaStream_t st) {
+static gpe_status launch_pass_t(const PassGeom<T>& G, int blocks, const PassData<T>& D, cudaStream_t st) {
+  using C = typename C2t<T>::type;
+  const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
+  const int nst = 1 + ((D.xsub || D.step_on_load) ? 1 : 0) + (D.acc_in ? 1 : 0);
+  const size_t smem = (size_t)G.F * sizeof(C) + 2 * (size_t)G.LC * G.P * sizeof(C) +
+                      (size_t)nst * G.LB * G.len * vsz;
   static size_t allowed = 0;
   if (smem > allowed) {
     allow_smem(k_pass<T, CPLX, EPI>, smem);
@@ -180,10 +192,9 @@ template <typename T>
 gpe_status launch_pass(const GridDev<T>& d, int axis, const PassData<T>& D, int cplx, int epi, cudaStream_t st) {
   const PassGeom<T>& G = d.geom[axis];
   const int nb = d.blocks[axis];
-  const size_t sm = d.smem[axis];
 #define GPE_PASS_CASE(E)                                                            \
   case E:                                                                           \
-    return cplx ? launch_pass_t<T, true, E>(G, nb, sm, D, st) : launch_pass_t<T, false, E>(G, nb, sm, D, st);
+    return cplx ? launch_pass_t<T, true, E>(G, nb, D, st) : launch_pass_t<T, false, E>(G, nb, D, st);
   switch (epi) {
     GPE_PASS_CASE(EPI_ACC)
     GPE_PASS_CASE(EPI_GRAD)
