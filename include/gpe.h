@@ -157,6 +157,12 @@ typedef struct {
                          when 40 steps bring no new smallest residual          [1e-6] */
   int chunk;          /* Algorithm 1 iterations queued between host checks      [16] */
   int use_graphs;     /* capture the queued iterations in CUDA graphs           [1] */
+  int persistent;     /* spectral grids: run each Algorithm 1 run as one
+                         cooperative persistent launch (grid barriers with
+                         bounded waits; GPE_ETIMEOUT if one expires)            [1] */
+  int cluster;        /* float32 Algorithm 1 on 2D Fourier grids: one thread-block
+                         cluster holds the whole state in distributed shared
+                         memory (grids up to 256^2 complex)                      [1] */
 } gpe_solve_opts;
 
 typedef struct {

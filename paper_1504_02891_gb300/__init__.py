@@ -78,7 +78,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("levels", C.c_int), ("mode", C.c_int), ("method", C.c_int), ("k_init", C.c_int),
                 ("k_sub", C.c_int), ("max_outer", C.c_int), ("max_iter", C.c_int), ("eps0", C.c_double),
                 ("delta_stop", C.c_double), ("res_tol", C.c_double), ("delta0", C.c_double),
-                ("switch_rel", C.c_double), ("chunk", C.c_int), ("use_graphs", C.c_int)]
+                ("switch_rel", C.c_double), ("chunk", C.c_int), ("use_graphs", C.c_int), ("persistent", C.c_int),
+                ("cluster", C.c_int)]
 
 
 class SolveReport(C.Structure):

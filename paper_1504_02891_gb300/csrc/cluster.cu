@@ -1,0 +1,417 @@
+// cluster.cu -- float32 Algorithm 1 on 2D Fourier grids with one thread-block
+// cluster per instance, the whole state in distributed shared memory.
+//
+// Why: at the cascade's grid sizes (<= 256^2 points) an operator application
+// is a latency chain, not a bandwidth problem.  A cluster of CS CTAs (2..16)
+// keeps X_cur, G_cur, the trial point, its gradient and the kinetic sum of
+// its rows in shared memory: each CTA owns n1/CS consecutive rows.  Per
+// Algorithm 1 iteration:
+//   1. Cayley step on the local rows (Theorem 3.3 coefficients);
+//   2. x-lines (local rows): FFT, line symbol, inverse FFT -> K = T_x Y;
+//   3. cluster barrier;
+//   4. y-lines (n0/CS columns per CTA): gather the columns of Y from every
+//      CTA's shared memory (DSMEM), FFT, symbol, inverse FFT, add T_y Y into
+//      the owners' K (DSMEM read-modify-write, one writer per element);
+//   5. cluster barrier;
+//   6. epilogue on the local rows (G = 2(K + V Y) + 4 alpha |Y|^2 Y and the
+//      float64 reduction terms, float pairs per thread), CTA partials;
+//   7. cluster barrier; every CTA folds the CS partials in rank order and runs
+//      the step-size control (alg1_control) on its own copy of the control
+//      block -- identical inputs, identical state, no further barrier.
+// Nothing goes to global memory until the run ends.  Cluster barriers are
+// hardware barriers; every CTA executes the same sequence of them because the
+// control decisions are bit-identical across the cluster.
+#include <cooperative_groups.h>
+#include "ops_impl.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gpe {
+
+
+
+// SHIFT = true: Algorithm 1 on the regularized Newton model W^(k) in
+// difference form.  The unknown is D = X - X^k, the gradient is kept as
+// G^ = grad W - theta_k X = P_k + H_k D + (delta - theta_k) D with
+// P_k = G_k - theta_k X^k (float64 on the host side, passed in float32), so
+// every float32 vector is small and nothing cancels.  The Cayley curve is the
+// same for G^ as for grad W (A(X) = G X^* - X G^* does not change when a real
+// multiple of X is added to G), so Theorem 3.3's coefficients apply to G^;
+// the step is D' = (a - 1) X^k + a D + b G^ with a - 1 formed without
+// cancellation.  The objective is the model decrease
+// Re<P_k, D> + theta_k Re<X^k, D> + 1/2 Re<D, H_k D> + delta/2 ||D||^2.
+template <bool CPLX, bool SHIFT>
+__global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
+  using V = typename VT<float, CPLX>::V;
+  using C = float2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int cs = A.cs;
+  const int cid = blockIdx.x >> A.logcs;
+  const int ncl = gridDim.x >> A.logcs;
+  const int logR = A.logn1 - A.logcs;      // rows per CTA = n1 / cs
+  const int R = 1 << logR;
+  const int Cc = A.n0 >> A.logcs;          // columns per CTA in the y-pass
+  const int n0 = A.n0, n1 = A.n1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int Pm = A.P0 > A.P1 ? A.P0 : A.P1;
+
+  extern __shared__ __align__(16) unsigned char sm[];
+  C* tw0 = reinterpret_cast<C*>(sm);
+  C* tw1 = tw0 + n0;
+  unsigned char* vb = reinterpret_cast<unsigned char*>(tw1 + n1);
+  constexpr int NVEC = SHIFT ? 7 : 5;
+  V* vec[NVEC];
+#pragma unroll
+  for (int i = 0; i < NVEC; ++i) vec[i] = reinterpret_cast<V*>(vb + (size_t)i * A.vec_bytes);  // X0 X1 G0 G1 K [Xk Pk]
+  float* Vs = reinterpret_cast<float*>(vb + (size_t)NVEC * A.vec_bytes);      // potential of the local rows
+  C* f0 = reinterpret_cast<C*>(vb + (size_t)NVEC * A.vec_bytes + A.vpot_bytes);
+  C* f1 = f0 + A.lch * Pm;
+  double* part = reinterpret_cast<double*>(f1 + A.lch * Pm);
+  __shared__ Alg1Ctl s_ctl;
+  __shared__ double s_res[NQ];
+  using Acc = DF;
+
+  for (int i = tid; i < n0; i += nt) tw0[i] = A.tw0[i];
+  for (int i = tid; i < n1; i += nt) tw1[i] = A.tw1[i];
+
+  const int nloc = R * n0;                 // local elements per vector
+  auto stamp = [&](int inst, int loop, int k) {
+    if (A.dbg && blockIdx.x == 0 && tid == 0 && inst == 0 && loop < A.dbg_n) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      A.dbg[loop * 8 + k] = t;
+    }
+  };
+  for (int inst = cid; inst < A.ninst; inst += ncl) {
+    const long long gbase = (long long)inst * n0 * n1 + (long long)rank * nloc;
+    const V* xin = reinterpret_cast<const V*>(A.x) + gbase;
+    const float* Vp = A.V + inst * A.vstride + (long long)rank * nloc;
+    const float om = A.omega ? A.omega[inst] : 0.f;
+    if (tid == 0) s_ctl = A.ctl[inst];
+    __syncthreads();
+    for (int i = tid; i < nloc; i += nt) {
+      if constexpr (SHIFT) {
+        vec[s_ctl.trial][i] = vzero<V>();           // D = 0: the trial point is X^k
+        vec[5][i] = reinterpret_cast<const V*>(A.xk)[gbase + i];
+        vec[6][i] = reinterpret_cast<const V*>(A.pk)[gbase + i];
+      } else {
+        vec[s_ctl.trial][i] = xin[i];
+      }
+      Vs[i] = Vp[i];
+    }
+    __syncthreads();
+
+    for (int loop = 0; loop < A.max_loops; ++loop) {
+      if (s_ctl.done) break;
+      stamp(inst, loop, 0);
+      const int trial = s_ctl.trial, cur = s_ctl.cur;
+      V* Xt = vec[trial];
+      V* Gt = vec[2 + trial];
+      V* K = vec[4];
+      const bool hc = s_ctl.has_cur != 0;
+      // 1. Cayley step on the local rows
+      if (hc) {
+        const V* Xc = vec[cur];
+        const V* Gc = vec[2 + cur];
+        if constexpr (SHIFT) {
+          const V* Xk = vec[5];
+          const float am1 = (float)s_ctl.am1, sa = (float)s_ctl.a, sb = (float)s_ctl.b;
+          for (int i = tid; i < nloc; i += nt) Xt[i] = am1 * Xk[i] + sa * Xc[i] + sb * Gc[i];
+        } else {
+          const float sa = (float)(s_ctl.s * s_ctl.a), sb = (float)(s_ctl.s * s_ctl.b);
+          for (int i = tid; i < nloc; i += nt) Xt[i] = sa * Xc[i] + sb * Gc[i];
+        }
+        __syncthreads();
+      }
+      stamp(inst, loop, 1);
+      // 2. x-lines of the local rows -> K
+      {
+        const int nlines = CPLX ? R : R / 2;
+        const float c2 = 0.5f / n0, c1 = om / n0, dl = A.dlam0;
+        for (int c0 = 0; c0 < nlines; c0 += A.lch) {
+          const int nl = min(A.lch, nlines - c0);
+          const int ndata = CPLX ? nl : 2 * nl;
+          for (int f = tid; f < ndata * n0; f += nt) {
+            const int l = f >> A.logn0, j = f & (n0 - 1);
+            const int row = (CPLX ? c0 : 2 * c0) + l;
+            const V v = Xt[row * n0 + j];
+            if constexpr (CPLX) f0[l * A.P0 + pidx(j)] = v;
+            else reinterpret_cast<float*>(f0 + (l >> 1) * A.P0)[2 * pidx(j) + (l & 1)] = v;
+          }
+          __syncthreads();
+          const int rowbase = rank * R + (CPLX ? c0 : 2 * c0);
+          auto sym = [&](int line, int m, C v) -> C {
+            const float lm = dl * (float)(m < (n0 >> 1) ? m : m - n0);
+            float sy = c2 * lm * lm;
+            if (CPLX) sy += c1 * A.yn[rowbase + line] * lm;
+            C r;
+            r.x = sy * v.x;
+            r.y = -sy * v.y;
+            return r;
+          };
+          C* r = fft_run<C>(f0, f1, A.logn0, nl, A.P0, tw0, sym);
+          C* o = fft_run<C>(r, r == f0 ? f1 : f0, A.logn0, nl, A.P0, tw0, PostNone());
+          for (int f = tid; f < ndata * n0; f += nt) {
+            const int l = f >> A.logn0, j = f & (n0 - 1);
+            const int row = (CPLX ? c0 : 2 * c0) + l;
+            V kv;
+            if constexpr (CPLX) {
+              const C ov = o[l * A.P0 + pidx(j)];
+              kv.x = ov.x;
+              kv.y = -ov.y;
+            } else {
+              const C ov = o[(l >> 1) * A.P0 + pidx(j)];
+              kv = (l & 1) ? -ov.y : ov.x;
+            }
+            K[row * n0 + j] = kv;
+          }
+          __syncthreads();
+        }
+      }
+      stamp(inst, loop, 2);
+      cl.sync();
+      stamp(inst, loop, 3);
+      // 4. y-lines of this CTA's columns: gather from every CTA, add T_y Y into the owners' K
+      {
+        const int nlines = CPLX ? Cc : Cc / 2;
+        const float c2 = 0.5f / n1, c1 = -om / n1, dl = A.dlam1;
+        for (int c0 = 0; c0 < nlines; c0 += A.lch) {
+          const int nl = min(A.lch, nlines - c0);
+          const int ndata = CPLX ? nl : 2 * nl;
+          const int logd = 31 - __clz(ndata);          // ndata is a power of two
+          const int colbase = rank * Cc + (CPLX ? c0 : 2 * c0);
+          for (int f = tid; f < ndata * n1; f += nt) {
+            const int l = f & (ndata - 1), y = f >> logd;
+            const int owner = y >> logR, lr = y & (R - 1);
+            const V* rem = cl.map_shared_rank(Xt, owner);
+            const V v = rem[lr * n0 + colbase + l];
+            if constexpr (CPLX) f0[l * A.P1 + pidx(y)] = v;
+            else reinterpret_cast<float*>(f0 + (l >> 1) * A.P1)[2 * pidx(y) + (l & 1)] = v;
+          }
+          __syncthreads();
+          auto sym = [&](int line, int m, C v) -> C {
+            const float lm = dl * (float)(m < (n1 >> 1) ? m : m - n1);
+            float sy = c2 * lm * lm;
+            if (CPLX) sy += c1 * A.xn[colbase + line] * lm;
+            C r;
+            r.x = sy * v.x;
+            r.y = -sy * v.y;
+            return r;
+          };
+          C* r = fft_run<C>(f0, f1, A.logn1, nl, A.P1, tw1, sym);
+          C* o = fft_run<C>(r, r == f0 ? f1 : f0, A.logn1, nl, A.P1, tw1, PostNone());
+          for (int f = tid; f < ndata * n1; f += nt) {
+            const int l = f & (ndata - 1), y = f >> logd;
+            const int owner = y >> logR, lr = y & (R - 1);
+            V kv;
+            if constexpr (CPLX) {
+              const C ov = o[l * A.P1 + pidx(y)];
+              kv.x = ov.x;
+              kv.y = -ov.y;
+            } else {
+              const C ov = o[(l >> 1) * A.P1 + pidx(y)];
+              kv = (l & 1) ? -ov.y : ov.x;
+            }
+            V* remk = cl.map_shared_rank(K, owner);
+            V* pk = remk + lr * n0 + colbase + l;
+            *pk = *pk + kv;
+          }
+          __syncthreads();
+        }
+      }
+      stamp(inst, loop, 4);
+      cl.sync();
+      stamp(inst, loop, 5);
+      // 6. epilogue on the local rows
+      Acc acc[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+      float amax = 0.f;
+      if constexpr (SHIFT) {
+        const float al = (float)s_ctl.alpha, de = (float)s_ctl.delta, thk = (float)s_ctl.theta_ref;
+        const float thc = (float)(hc ? s_ctl.theta_c : s_ctl.theta_hint);
+        const V* Xk = vec[5];
+        const V* Pk = vec[6];
+        const V* Xc = hc ? vec[cur] : nullptr;
+        const V* Gc = hc ? vec[2 + cur] : nullptr;
+        for (int i = tid; i < nloc; i += nt) {
+          const V y = Xt[i], xk = Xk[i], pk = Pk[i];
+          const V lin = K[i] + Vs[i] * y;
+          const float x2 = tre(xk, xk), R = tre(xk, y);
+          const V hD = 2.f * lin + (4.f * al) * (x2 * y + (2.f * R) * xk);
+          const V gh = pk + hD + (de - thk) * y;
+          Gt[i] = gh;
+          const V x = xk + y;
+          acc_add(acc[Q_WX], tre(pk, y) + thk * R + 0.5f * tre(y, hD) + 0.5f * de * tre(y, y));
+          acc_add(acc[Q_NY], tre(x, x));
+          acc_add(acc[Q_YG], tre(x, gh));
+          acc_add(acc[Q_GG], tre(gh, gh));
+          const V q = gh - thc * x;
+          acc_add(acc[Q_Q], tre(q, q));
+          acc_add(acc[Q_QY], tre(q, x));
+          const V yc = Xc ? Xc[i] : vzero<V>();
+          const V gc = Gc ? Gc[i] : vzero<V>();
+          const V sv = y - yc;
+          const V vv = (gh - gc) - thc * sv;
+          const float s2 = tre(sv, sv);
+          acc_add(acc[Q_SS], s2);
+          acc_add(acc[Q_SV], tre(sv, vv));
+          acc_add(acc[Q_VV], tre(vv, vv));
+          acc_add(acc[Q_VY], tre(vv, x));
+          acc_add(acc[Q_SY], tre(sv, x));
+          amax = fmaxf(amax, s2);
+        }
+      } else {
+        EpiCtx<float, CPLX> E;
+        E.out = Gt;
+        E.xc = hc ? vec[cur] : nullptr;
+        E.gc = hc ? vec[2 + cur] : nullptr;
+        E.base = nullptr;
+        E.gk = nullptr;
+        E.nl = (float)s_ctl.alpha;
+        E.shift = 0.f;
+        E.lin_scale = 2.f;
+        E.th_c = (float)(hc ? s_ctl.theta_c : s_ctl.theta_hint);
+        E.delta = 0.f;
+        for (int i = tid; i < nloc; i += nt) {
+          const V y = Xt[i];
+          const V lin = K[i] + Vs[i] * y;
+          epilogue_point<float, CPLX, EPI_F, false>(E, i, y, lin, acc, amax);
+        }
+      }
+      block_partial(acc, amax, NQ, part);
+      stamp(inst, loop, 6);
+      cl.sync();
+      // 7. fold the cluster's partials in rank order, then the control on the local copy
+      if (tid < NQ) {
+        const int q = tid;
+        DF v;
+        acc_zero(v);
+        for (int r = 0; r < cs; ++r) {
+          const DF* rp = reinterpret_cast<const DF*>(cl.map_shared_rank(part, r));
+          const DF w = rp[q];
+          if (q == Q_MAX) v.hi = fmaxf(v.hi, w.hi);
+          else acc_merge(v, w);
+        }
+        s_res[q] = acc_value(v);
+      }
+      __syncthreads();
+      if (tid == 0) alg1_control(&s_ctl, s_res);
+      __syncthreads();
+      stamp(inst, loop, 7);
+    }
+    // write back the current point and its gradient, the control block and the sums
+    {
+      V* xo = reinterpret_cast<V*>(A.x) + gbase;
+      V* go = A.g ? reinterpret_cast<V*>(A.g) + gbase : nullptr;
+      const V* Xc = vec[s_ctl.cur];
+      const V* Gc = vec[2 + s_ctl.cur];
+      for (int i = tid; i < nloc; i += nt) {
+        xo[i] = Xc[i];
+        if (go) go[i] = Gc[i];
+      }
+      if (rank == 0 && tid == 0) A.ctl[inst] = s_ctl;
+      if (rank == 0 && tid < NQ) A.results[(size_t)inst * NQ + tid] = s_res[tid];
+    }
+    cl.sync();   // no CTA reuses or leaves its shared memory while others may read it
+  }
+}
+
+// Cluster size, chunk and shared memory for an n0 x n1 grid; false if the
+// state does not fit in a 16-CTA cluster.
+bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs_out, int* lch_out, int* P0, int* P1, size_t* smem_out,
+                   unsigned int* vec_bytes, unsigned int* vpot_bytes) {
+  const size_t vsz = cplx ? 8 : 4;
+  const size_t total = (size_t)n0 * n1 * vsz;
+  // smallest cluster whose per-CTA share of a vector is <= 16 KiB (more CTAs
+  // share the FFT work), else the largest that fits
+  int pick = -1;
+  for (int cs = 1; cs <= 16; cs *= 2) {
+    if (n1 / cs < (cplx ? 1 : 2) || n0 / cs < (cplx ? 1 : 2)) break;
+    if (total / cs <= 16 * 1024) { pick = cs; break; }
+    if (total / cs <= 48 * 1024) pick = cs;
+  }
+  if (pick < 0) return false;
+  const int cs = pick;
+  const int R = n1 / cs, Cc = n0 / cs;
+  const int lines = std::max(cplx ? R : R / 2, cplx ? Cc : Cc / 2);
+  const int Fm = std::max(n0, n1);
+  int lch = 1;
+  while (lch * 2 <= lines && lch * 2 * Fm <= 4096) lch *= 2;
+  const int p0 = n0 + n0 / 16 + 1, p1 = n1 + n1 / 16 + 1;
+  const size_t vb = ((size_t)R * n0 * vsz + 15) & ~(size_t)15;
+  const size_t vp = ((size_t)R * n0 * 4 + 15) & ~(size_t)15;
+  auto need = [&](int lc) {
+    return (size_t)(n0 + n1) * 8 + nvec * vb + vp + 2 * (size_t)lc * std::max(p0, p1) * 8 + NQ * 8;
+  };
+  while (lch > 1 && need(lch) > 200 * 1024) lch /= 2;
+  const size_t smem = need(lch);
+  if (smem > 200 * 1024) return false;
+  *cs_out = cs;
+  *lch_out = lch;
+  *P0 = p0;
+  *P1 = p1;
+  *smem_out = smem;
+  *vec_bytes = (unsigned int)vb;
+  *vpot_bytes = (unsigned int)vp;
+  return true;
+}
+
+static int ilog2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Launch the cluster engine for `ninst` instances of one grid; clusters loop
+// over instances.  Returns GPE_EINVAL if the grid does not fit (callers then
+// use the CTA-grid path).
+gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st) {
+  int cs, lch, P0, P1;
+  size_t smem;
+  unsigned int vb, vp;
+  if (!cluster_shape(A.n0, A.n1, cplx, A.shifted ? 7 : 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp))
+    return fail(GPE_EINVAL, "grid too large for the cluster engine");
+  A.cs = cs;
+  A.logcs = ilog2i(cs);
+  A.logn0 = ilog2i(A.n0);
+  A.logn1 = ilog2i(A.n1);
+  A.lch = lch;
+  A.P0 = P0;
+  A.P1 = P1;
+  A.vec_bytes = vb;
+  A.vpot_bytes = vp;
+  const void* fn = A.shifted ? (cplx ? (const void*)k_cluster_alg1<true, true> : (const void*)k_cluster_alg1<false, true>)
+                             : (cplx ? (const void*)k_cluster_alg1<true, false> : (const void*)k_cluster_alg1<false, false>);
+  GPE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (cs > 8) GPE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int maxc = 0;
+  cfg.gridDim = dim3(cs);
+  GPE_CUDA(cudaOccupancyMaxActiveClusters(&maxc, fn, &cfg));
+  if (maxc < 1) return fail(GPE_EINVAL, "no cluster of this shape fits on the device");
+  const int ncl = std::min(A.ninst, maxc);
+  cfg.gridDim = dim3(cs * ncl);
+  ProfScope ps(kernel_name("cluster_alg1", 0, cplx, -1, (long long)A.n0 * A.n1), st);
+  if (A.shifted) {
+    if (cplx) GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<true, true>, A));
+    else GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<false, true>, A));
+  } else {
+    if (cplx) GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<true, false>, A));
+    else GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<false, false>, A));
+  }
+  return GPE_OK;
+}
+
+}  // namespace gpe

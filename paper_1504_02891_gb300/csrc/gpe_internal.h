@@ -93,12 +93,30 @@ template <typename Ti, typename To>
 gpe_status launch_convert(const Ti* in, To* out, long long n, double scale, cudaStream_t st);
 gpe_status launch_step_coef(const double* mom, int nbatch, double h, double tau, double* coef, cudaStream_t st);
 gpe_status launch_norm_coef(const double* mom, int nbatch, double h, double* coef, cudaStream_t st);
+gpe_status launch_to_shifted_f32(const double* xk, const double* gk, double th, float* xk32, float* pk32, long long n,
+                                 cudaStream_t st);
+gpe_status launch_add_f32_to_f64(const double* xk, const float* d, double* z, long long n, cudaStream_t st);
 
 // One operator application: the per-axis passes (or the FD stencil) with the
 // epilogue `epi` on the last pass.  acc is a scratch vector of the grid's size.
 template <typename T>
 gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int epi, void* acc, bool step_first,
                     cudaStream_t st);
+
+template <typename T>
+gpe_status persist_config(const GridHost& g, const GridDev<T>& d, int epi, int* grid, size_t* smem);
+template <typename T>
+gpe_status launch_alg1_persist(const GridHost& g, const GridDev<T>& d, const PassData<T>& D, void* acc,
+                               unsigned int* bar, int* err, int max_loops, int epi, int grid, size_t smem,
+                               cudaStream_t st);
+
+// GPE_PERSIST_TRACE=1: phase timestamps of persistent launches (debug aid).
+unsigned long long* persist_debug_buffer(int* n);
+void persist_debug_report(cudaStream_t st, long long M, int f64);
+
+gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st);
+bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs, int* lch, int* P0, int* P1, size_t* smem,
+                   unsigned int* vec_bytes, unsigned int* vpot_bytes);
 
 void destroy_solver_cache(void* cache);
 

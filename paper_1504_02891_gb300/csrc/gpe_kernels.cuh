@@ -66,9 +66,13 @@ struct Alg1Ctl {
   int k, m, nfe, accepted_last;
   double tau, C, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;
   double a, b, s;      // Cayley step coefficients of the next trial
+  double am1;          // a - 1 without cancellation (shifted subproblem form)
+  double theta_ref;    // shifted form: theta_k of the outer iterate
   double res;          // ||A(X)X||_2 of the current point
   double best_res;     // smallest res seen (stagnation test)
   int k_best, stall_iters;   // stop after stall_iters accepted steps without a new best (0 = off)
+  int two_slots;       // 1: slots cur/trial swap on acceptance (no third slot)
+  int pad1;
 };
 
 // Outer state of Algorithm 2 (ratio test), written by the ratio pass.
@@ -138,6 +142,53 @@ struct PassData {
   unsigned int* ticket;
   int nq;               // active slots (0: none)
   int control;          // 0: none, 1: Algorithm 1 control, 2: ratio control
+};
+
+// Arguments of the cluster engine (float32 Algorithm 1, 2D Fourier grids, one
+// thread-block cluster per instance).
+struct ClusterArgs {
+  int n0, n1;              // x extent (row length) and y extent (rows), powers of two
+  int logn0, logn1;
+  int cs, logcs;           // cluster size
+  int ninst;               // instances
+  int max_loops;           // bound on Algorithm 1 trials per instance
+  int lch;                 // complex lines per FFT chunk (power of two)
+  int P0, P1;              // padded row pitches of the FFT buffers (n0 and n1 lines)
+  float dlam0, dlam1;      // 2 pi / L per axis
+  const float* V;          // potential [ninst or 1][n1][n0]
+  long long vstride;       // instance stride of V (0 = shared)
+  const float* xn;         // x nodes [n0]
+  const float* yn;         // y nodes [n1]
+  const float* omega;      // Omega per instance (null: 0)
+  const float2* tw0;       // e^{-2 pi i k / n0}
+  const float2* tw1;       // e^{-2 pi i k / n1}
+  void* x;                 // [ninst][n1][n0]: X0 in (unit norm), final X out
+  void* g;                 // [ninst][n1][n0]: final G out (may be null)
+  Alg1Ctl* ctl;            // [ninst], phase 0 prepared by the host
+  double* results;         // [ninst][NQ] sums of the final evaluation
+  unsigned int vec_bytes;  // bytes of one CTA's share of a vector (16-byte multiple)
+  unsigned int vpot_bytes; // bytes of the CTA's rows of the potential (float32, 16-byte multiple)
+  unsigned long long* dbg; // optional phase timestamps (CTA 0, first instance): [loop][8]
+  int dbg_n;
+  int shifted;             // 1: regularized Newton subproblem in difference form (see cluster.cu)
+  const void* xk;          // shifted: X^k (float32) [ninst][n1][n0]
+  const void* pk;          // shifted: P_k = G_k - theta_k X^k (float32)
+};
+
+// Arguments of the persistent Algorithm 1 kernel.
+template <typename T>
+struct PersistArgs {
+  PassGeom<T> G[3];
+  int blocks[3];        // tiles (x instances) of each axis pass
+  int dim;
+  PassData<T> D;        // solver data (slots, control block, reduction scratch)
+  void* acc;            // kinetic accumulator
+  unsigned int* bar;    // grid barrier: [0] arrivals, [1] generation
+  int* err;             // set when a barrier wait gave up
+  int max_loops;        // bound on the iterations (accepted + rejected trials)
+  size_t tw_bytes;      // twiddle tables of all axes at the front of shared memory (16-byte multiple)
+  unsigned long long* dbg;   // optional phase timestamps (globaltimer, CTA 0): [loop][4]
+  int dbg_n;
 };
 
 }  // namespace gpe

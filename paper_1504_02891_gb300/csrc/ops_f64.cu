@@ -31,3 +31,19 @@ gpe_status launch_norm_coef(const double* mom, int nbatch, double h, double* coe
   return GPE_OK;
 }
 }  // namespace gpe
+
+namespace gpe {
+gpe_status launch_to_shifted_f32(const double* xk, const double* gk, double th, float* xk32, float* pk32, long long n,
+                                 cudaStream_t st) {
+  ProfScope ps("to_shifted_f32", st);
+  k_to_shifted_f32<<<ew_blocks(n), NTHREADS, 0, st>>>(xk, gk, th, xk32, pk32, n);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
+}
+gpe_status launch_add_f32_to_f64(const double* xk, const float* d, double* z, long long n, cudaStream_t st) {
+  ProfScope ps("add_f32_to_f64", st);
+  k_add_f32_to_f64<<<ew_blocks(n), NTHREADS, 0, st>>>(xk, d, z, n);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
+}
+}  // namespace gpe

@@ -2,6 +2,7 @@
 // ops_f32.cu and ops_f64.cu.  See gpe_kernels.cuh for the design summary.
 #pragma once
 #include <math.h>
+#include <type_traits>
 #include "gpe_kernels.cuh"
 #include "gpe_internal.h"
 
@@ -329,85 +330,175 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ----------------------------------------------------------------- block reductions
-// Reduce the per-thread sums acc[0..nq) and the max slot acc_max over the
-// block, write this CTA's float64 partials, and let the last CTA fold all
-// partials per instance in a fixed order into results[inst][q] (deterministic).
-// Slots >= nq (other than Q_MAX) are written as 0.  Returns true in the last
-// CTA (all threads).
-template <typename A>
-static __device__ bool reduce_partials(A (&acc)[NQ], double acc_max, int nq, double* partials, double* results,
-                                       unsigned int* ticket, int tiles_per_inst) {
-  __shared__ double red[NTHREADS / 32][NQ];
-  __shared__ int s_last;
+// Partials are NQ slots of 8 bytes per CTA: float64 in float64 kernels, float
+// pairs (hi, lo) in float32 kernels, so that a float32 reduction never touches
+// the float64 pipe until its final NQ values.
+__device__ __forceinline__ void df_max(DF& a, const DF& b) { a.hi = fmaxf(a.hi, b.hi); }
+
+// Reduce the per-thread sums acc[0..nq) and the max slot over the block and
+// write this CTA's partials to out[0..NQ) (slots >= nq other than Q_MAX as 0).
+// Ends with a barrier.
+template <typename A, typename M>
+static __device__ void block_partial(A (&acc)[NQ], M amax2, int nq, double* out) {
+  const double acc_max = sqrt((double)amax2);   // amax2 is the largest |.|^2 of the CTA's points
+  __shared__ A red[NTHREADS / 32][NQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
+    A v;
     if (q == Q_MAX) {
-      double v = acc_max;
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-      if (lane == 0) red[warp][q] = v;
+      if constexpr (sizeof(A) == sizeof(DF) && !std::is_same<A, double>::value) {
+        v.hi = (float)acc_max;
+        v.lo = 0.f;
+        for (int o = 16; o > 0; o >>= 1) v.hi = fmaxf(v.hi, __shfl_down_sync(0xffffffffu, v.hi, o));
+      } else {
+        v = acc_max;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+      }
     } else if (q < nq) {
-      A v = acc[q];
+      v = acc[q];
       for (int o = 16; o > 0; o >>= 1) acc_merge(v, shfl_down(v, o));
-      if (lane == 0) red[warp][q] = acc_value(v);
-    } else if (lane == 0) {
-      red[warp][q] = 0.0;
+    } else {
+      acc_zero(v);
     }
+    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
   if (threadIdx.x < NQ) {
     const int q = threadIdx.x;
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v = (q == Q_MAX) ? fmax(v, red[w][q]) : v + red[w][q];
-    partials[(size_t)blockIdx.x * NQ + q] = v;
+    A v = red[0][q];
+    for (int w = 1; w < nw; ++w) {
+      if constexpr (std::is_same<A, double>::value) v = (q == Q_MAX) ? fmax(v, red[w][q]) : v + red[w][q];
+      else {
+        if (q == Q_MAX) df_max(v, red[w][q]);
+        else acc_merge(v, red[w][q]);
+      }
+    }
+    reinterpret_cast<A*>(out)[q] = v;
   }
-  __threadfence();
   __syncthreads();
+}
+
+// Fold the partials of `tiles` consecutive CTAs (fixed order) into float64
+// out[0..NQ).  Called by one whole CTA.  Ends with a barrier.
+template <typename A>
+static __device__ void fold_partials(const double* partials, int tiles, int nq, double* out) {
+  __shared__ A red[NTHREADS / 32][NQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  A v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc_zero(v[q]);
+  const A* pp = reinterpret_cast<const A*>(partials);
+  for (int i = threadIdx.x; i < tiles; i += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (q >= nq && q != Q_MAX) continue;
+      A w;
+      if constexpr (std::is_same<A, double>::value) {
+        w = __ldcg(pp + (size_t)i * NQ + q);
+        v[q] = (q == Q_MAX) ? fmax(v[q], w) : v[q] + w;
+      } else {
+        const float2 f = __ldcg(reinterpret_cast<const float2*>(pp + (size_t)i * NQ + q));
+        w.hi = f.x;
+        w.lo = f.y;
+        if (q == Q_MAX) df_max(v[q], w);
+        else acc_merge(v[q], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    A x = v[q];
+    if (q < nq || q == Q_MAX) {
+      for (int o = 16; o > 0; o >>= 1) {
+        if constexpr (std::is_same<A, double>::value) {
+          const double w = __shfl_down_sync(0xffffffffu, x, o);
+          x = (q == Q_MAX) ? fmax(x, w) : x + w;
+        } else {
+          const DF w = shfl_down(x, o);
+          if (q == Q_MAX) df_max(x, w);
+          else acc_merge(x, w);
+        }
+      }
+    } else {
+      acc_zero(x);
+    }
+    if (lane == 0) red[warp][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int q = threadIdx.x;
+    A x = red[0][q];
+    for (int w = 1; w < nw; ++w) {
+      if constexpr (std::is_same<A, double>::value) x = (q == Q_MAX) ? fmax(x, red[w][q]) : x + red[w][q];
+      else {
+        if (q == Q_MAX) df_max(x, red[w][q]);
+        else acc_merge(x, red[w][q]);
+      }
+    }
+    out[q] = acc_value(x);
+  }
+  __syncthreads();
+}
+
+// Block partial, then the last CTA to finish (atomic ticket) folds all
+// partials per instance into results[inst][q].  Returns true in the last CTA.
+template <typename A, typename M>
+static __device__ bool reduce_partials(A (&acc)[NQ], M amax2, int nq, double* partials, double* results,
+                                       unsigned int* ticket, int tiles_per_inst) {
+  __shared__ int s_last;
+  block_partial(acc, amax2, nq, partials + (size_t)blockIdx.x * NQ);
+  __threadfence();
   if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
   const int ninst = gridDim.x / tiles_per_inst;
-  for (int b = 0; b < ninst; ++b) {
-    double v[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-    for (int i = threadIdx.x; i < tiles_per_inst; i += blockDim.x) {
-      const double* p = partials + ((size_t)b * tiles_per_inst + i) * NQ;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        if (q >= nq && q != Q_MAX) continue;
-        const double w = __ldcg(p + q);
-        v[q] = (q == Q_MAX) ? fmax(v[q], w) : v[q] + w;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      if (q >= nq && q != Q_MAX) {
-        if (lane == 0) red[warp][q] = 0.0;
-        continue;
-      }
-      double x = v[q];
-      for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_down_sync(0xffffffffu, x, o);
-        x = (q == Q_MAX) ? fmax(x, w) : x + w;
-      }
-      if (lane == 0) red[warp][q] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < NQ) {
-      const int q = threadIdx.x;
-      double x = 0.0;
-      for (int w = 0; w < nw; ++w) x = (q == Q_MAX) ? fmax(x, red[w][q]) : x + red[w][q];
-      results[(size_t)b * NQ + q] = x;
-    }
-    __syncthreads();
-  }
+  for (int b = 0; b < ninst; ++b)
+    fold_partials<A>(partials + (size_t)b * tiles_per_inst * NQ, tiles_per_inst, nq, results + (size_t)b * NQ);
   if (threadIdx.x == 0) *ticket = 0u;
   __threadfence();
   __syncthreads();
   return true;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch: arrival counter
+// bar[0] and generation bar[1].  Every wait is bounded: after ~2^22 polls
+// (about a second) the CTA sets *err and returns false, and so does every CTA
+// that later sees *err set.
+static __device__ bool grid_barrier(unsigned int* bar, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = bar + 1;
+    volatile int* verr = err;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == gen) {
+        if (*verr) { ok = 0; break; }
+        if (++polls > (1LL << 22)) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (*verr) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // ----------------------------------------------------------------- solver control
@@ -425,6 +516,7 @@ static __device__ void set_coef(Alg1Ctl* c) {
   c->a = a;
   c->b = b;
   c->s = s;
+  c->am1 = (2.0 * t * XG - 2.0 * t * t * nxpp) / den;   // a - 1
 }
 
 // Algorithm 1 after an evaluation at the trial point: the nonmonotone test of
@@ -461,7 +553,12 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
   const double SS = r[Q_SS];
   const double SW = r[Q_SV] - dth * r[Q_SY];
   const double WW = r[Q_VV] - 2.0 * dth * r[Q_VY] + dth * dth * nY;
-  if (c->has_cur) {
+  if (c->two_slots) {
+    const int oc = c->has_cur ? c->cur : 1 - c->trial;
+    c->cur = c->trial;
+    c->trial = oc;
+    c->prev = oc;
+  } else if (c->has_cur) {
     const int oc = c->cur, op = c->prev, tr = c->trial;
     c->prev = oc;
     c->cur = tr;
@@ -538,6 +635,18 @@ static __device__ void rn_control(RNCtl* c, const double* r) {
   c->delta = fmin(fmax(nd, c->delta_min), c->delta_max);
 }
 
+// ----------------------------------------------------------------- coherent loads
+// Inside a persistent launch, data written by other CTAs during the same launch
+// must bypass the (non-coherent) L1: ld.global.cg.
+template <bool COH, typename X> __device__ __forceinline__ X ldv(const X* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+template <bool COH, typename X> __device__ __forceinline__ X rdc(const X& r) {
+  if constexpr (COH) return *(const volatile X*)&r;
+  else return r;
+}
+
 // ----------------------------------------------------------------- pointwise epilogue
 template <typename T, bool CPLX>
 struct EpiCtx {
@@ -550,10 +659,10 @@ struct EpiCtx {
   T nl, shift, lin_scale, th_c, delta;
 };
 
-template <typename T, bool CPLX, int EPI, typename A>
+template <typename T, bool CPLX, int EPI, bool COH = false, typename A>
 __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long long gi,
                                                typename VT<T, CPLX>::V x,
-                                               typename VT<T, CPLX>::V lin, A (&acc)[NQ], double& amax) {
+                                               typename VT<T, CPLX>::V lin, A (&acc)[NQ], T& amax) {
   using V = typename VT<T, CPLX>::V;
   if (EPI == EPI_GRAD) {
     const T x2 = tre(x, x);
@@ -562,7 +671,7 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     acc_add(acc[1], x2 * x2);
     acc_add(acc[2], x2);
   } else if (EPI == EPI_HESS) {
-    const V p = E.base[gi];
+    const V p = ldv<COH>(E.base + gi);
     const T p2 = tre(p, p);
     const T R = tre(p, x);
     E.out[gi] = lin + E.nl * (p2 * x + (T(2) * R) * p) + E.shift * x;
@@ -572,7 +681,7 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     if (EPI == EPI_F) {
       g = E.lin_scale * lin + (T(4) * E.nl * tre(y, y)) * y;
     } else {
-      const V xk = E.base[gi];
+      const V xk = ldv<COH>(E.base + gi);
       const V dd = y - xk;
       const T x2 = tre(xk, xk);
       const T R = tre(xk, dd);
@@ -590,8 +699,8 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     const V q = g - E.th_c * y;
     acc_add(acc[Q_Q], tre(q, q));
     acc_add(acc[Q_QY], tre(q, y));
-    const V xc = E.xc ? E.xc[gi] : vzero<V>();
-    const V gc = E.gc ? E.gc[gi] : vzero<V>();
+    const V xc = E.xc ? ldv<COH>(E.xc + gi) : vzero<V>();
+    const V gc = E.gc ? ldv<COH>(E.gc + gi) : vzero<V>();
     const V s = y - xc;
     const V v = (g - gc) - E.th_c * s;
     const T s2 = tre(s, s);
@@ -600,11 +709,11 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     acc_add(acc[Q_VV], tre(v, v));
     acc_add(acc[Q_VY], tre(v, y));
     acc_add(acc[Q_SY], tre(s, y));
-    amax = fmax(amax, (double)sqrt(s2));
+    amax = fmax(amax, s2);
   } else if (EPI == EPI_RATIO) {
     const V d = x;
-    const V xk = E.base[gi];
-    const V gk = E.gk[gi];
+    const V xk = ldv<COH>(E.base + gi);
+    const V gk = ldv<COH>(E.gk + gi);
     const T x2 = tre(xk, xk);
     const V ax = gk - (T(4) * E.nl * x2) * xk;
     const V z = xk + d;
@@ -616,11 +725,11 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     acc_add(acc[R_R2], R * R);
     acc_add(acc[R_DD], d2);
     acc_add(acc[R_GD], tre(gk, d));
-    amax = fmax(amax, (double)sqrt(d2));
+    amax = fmax(amax, d2);
   }
 }
 
-template <typename T, bool CPLX, int EPI>
+template <typename T, bool CPLX, int EPI, bool COH = false>
 __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& D) {
   using V = typename VT<T, CPLX>::V;
   E.out = (V*)D.out;
@@ -635,16 +744,16 @@ __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& 
   E.delta = T(0);
   if (D.ctl) {
     const Alg1Ctl* c = D.ctl;
-    E.nl = (T)c->alpha;
-    E.delta = (T)c->delta;
+    E.nl = (T)rdc<COH>(c->alpha);
+    E.delta = (T)rdc<COH>(c->delta);
     if (D.use_slots) {
-      E.out = (V*)D.gs[c->trial];
-      if (c->has_cur) {
-        E.xc = (const V*)D.xs[c->cur];
-        E.gc = (const V*)D.gs[c->cur];
-        E.th_c = (T)c->theta_c;
+      E.out = (V*)D.gs[rdc<COH>(c->trial)];
+      if (rdc<COH>(c->has_cur)) {
+        E.xc = (const V*)D.xs[rdc<COH>(c->cur)];
+        E.gc = (const V*)D.gs[rdc<COH>(c->cur)];
+        E.th_c = (T)rdc<COH>(c->theta_c);
       } else {
-        E.th_c = (T)c->theta_hint;
+        E.th_c = (T)rdc<COH>(c->theta_hint);
       }
     }
   }
@@ -686,18 +795,20 @@ __device__ __forceinline__ void visit_tile(const PassGeom<T>& G, const long long
   }
 }
 
-template <typename T, bool CPLX, int EPI>
-__global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D) {
+// One tile of one axis pass: load (asynchronous copies, or L2-coherent loads
+// inside a persistent launch), forward FFT with the fused symbol, inverse FFT,
+// epilogue into acc/amax.  blk = instance * tiles + tile.  Ends with a barrier.
+template <typename T, bool CPLX, int EPI, bool COH, typename A>
+__device__ __forceinline__ void pass_tile(const PassGeom<T>& G, const PassData<T>& D, int blk,
+                                          unsigned char* smem_raw, long long* s_off, T* s_rc, A (&acc)[NQ],
+                                          T& amax,
+                                          const typename C2t<T>::type* tw_pre = nullptr) {
   using C = typename C2t<T>::type;
   using V = typename VT<T, CPLX>::V;
-  if (D.ctl && D.ctl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ long long s_off[MAXLB];
-  __shared__ T s_rc[MAXLB];
   const int F = G.F, Pt = G.P;
   const int nt = blockDim.x, tid = threadIdx.x;
-  const int inst = blockIdx.x / G.tiles;
-  const int tile = blockIdx.x - inst * G.tiles;
+  const int inst = blk / G.tiles;
+  const int tile = blk - inst * G.tiles;
 
   // operands: src0 (input, or X_cur for the Cayley step), src1 (x_sub or G_cur), acc_in
   const V* xin = (const V*)D.x;
@@ -706,13 +817,16 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
   T sa = 0, sb = 0;
   if (D.use_slots) {
     const Alg1Ctl* c = D.ctl;
-    xin = (const V*)D.xs[c->trial];
+    const int trial = rdc<COH>(c->trial);
+    xin = (const V*)D.xs[trial];
     if (D.step_on_load) {
-      yst = (V*)D.xs[c->trial];
-      xin = (const V*)D.xs[c->cur];
-      src1 = (const V*)D.gs[c->cur];
-      sa = (T)(c->s * c->a);
-      sb = (T)(c->s * c->b);
+      const int cur = rdc<COH>(c->cur);
+      yst = (V*)D.xs[trial];
+      xin = (const V*)D.xs[cur];
+      src1 = (const V*)D.gs[cur];
+      const double cs = rdc<COH>(c->s);
+      sa = (T)(cs * rdc<COH>(c->a));
+      sb = (T)(cs * rdc<COH>(c->b));
     }
   }
   const V* accin = (const V*)D.acc_in;
@@ -723,6 +837,10 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
   V* st0 = reinterpret_cast<V*>(buf1 + G.LC * Pt);
   V* st1 = st0 + tile_n;
   V* st2 = st1 + (src1 ? tile_n : 0);
+  // potential of the tile (final passes only), staged with the other operands
+  T* stv = reinterpret_cast<T*>(st2 + (accin ? tile_n : 0));
+  const bool want_v = EPI != EPI_ACC;
+  const long long vbase = (long long)inst * G.M;
 
   for (int l = tid; l < G.LB; l += nt) {
     long long b;
@@ -731,17 +849,33 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
     s_off[l] = ok ? b : -1;
     if (G.rcoord) s_rc[l] = G.rcoord[ok ? ri : 0];
   }
-  for (int i = tid; i < F; i += nt) cp_async(tw_s + i, G.tw + i);
+  // twiddle table (read-only): preloaded by the caller, or an asynchronous
+  // copy, or plain loads when the tile loads below are not asynchronous
+  if (!tw_pre) {
+    for (int i = tid; i < F; i += nt) {
+      if constexpr (COH) tw_s[i] = G.tw[i];
+      else cp_async(tw_s + i, G.tw + i);
+    }
+  }
+  const C* twx = tw_pre ? tw_pre : tw_s;
   __syncthreads();
   // the whole tile (and the operands the epilogue needs) in flight at once
   visit_tile(G, s_off, [&](int l, int j, long long gi) {
     const int q = G.axis == 0 ? l * G.len + j : j * G.LB + l;
-    cp_async(st0 + q, xin + gi);
-    if (src1) cp_async(st1 + q, src1 + gi);
-    if (accin) cp_async(st2 + q, accin + gi);
+    if constexpr (COH) {
+      st0[q] = __ldcg(xin + gi);
+      if (src1) st1[q] = __ldcg(src1 + gi);
+      if (accin) st2[q] = __ldcg(accin + gi);
+      if (want_v) stv[q] = D.V[gi - vbase];
+    } else {
+      cp_async(st0 + q, xin + gi);
+      if (src1) cp_async(st1 + q, src1 + gi);
+      if (accin) cp_async(st2 + q, accin + gi);
+      if (want_v) cp_async(stv + q, D.V + (gi - vbase));
+    }
   });
   for (int i = tid; i < G.LC * Pt; i += nt) buf0[i] = mk<C>(0.0, 0.0);
-  cp_async_wait_all();
+  if constexpr (!COH) cp_async_wait_all();
   __syncthreads();
 
   visit_tile(G, s_off, [&](int l, int j, long long gi) {
@@ -779,16 +913,11 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
     r.y = -sym * v.y;
     return r;
   };
-  C* r = fft_run<C>(buf0, buf1, G.logF, G.LC, Pt, tw_s, symbol);
-  C* o = fft_run<C>(r, r == buf0 ? buf1 : buf0, G.logF, G.LC, Pt, tw_s, PostNone());
+  C* r = fft_run<C>(buf0, buf1, G.logF, G.LC, Pt, twx, symbol);
+  C* o = fft_run<C>(r, r == buf0 ? buf1 : buf0, G.logF, G.LC, Pt, twx, PostNone());
 
   EpiCtx<T, CPLX> E;
-  if (EPI != EPI_ACC) make_ctx<T, CPLX, EPI>(E, D);
-  using A = typename AccT<T>::type;
-  A acc[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
-  double amax = 0.0;
+  if (EPI != EPI_ACC) make_ctx<T, CPLX, EPI, COH>(E, D);
   const long long ibase = inst * G.M;
   visit_tile(G, s_off, [&](int l, int j, long long gi) {
     const int q = G.axis == 0 ? l * G.len + j : j * G.LB + l;
@@ -808,11 +937,119 @@ __global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D)
       return;
     }
     const V x = st0[q];
-    const V lin = kin + D.V[gi - ibase] * x;
-    epilogue_point<T, CPLX, EPI>(E, gi, x, lin, acc, amax);
+    const V lin = kin + stv[q] * x;
+    epilogue_point<T, CPLX, EPI, COH>(E, gi, x, lin, acc, amax);
   });
+  __syncthreads();
+}
+
+template <typename T, bool CPLX, int EPI>
+__global__ void __launch_bounds__(NTHREADS) k_pass(PassGeom<T> G, PassData<T> D) {
+  if (D.ctl && D.ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_off[MAXLB];
+  __shared__ T s_rc[MAXLB];
+  using A = typename AccT<T>::type;
+  A acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+  T amax = T(0);
+  pass_tile<T, CPLX, EPI, false>(G, D, blockIdx.x, smem_raw, s_off, s_rc, acc, amax);
   if (EPI == EPI_ACC || EPI == EPI_HESS || D.nq == 0) return;
   if (reduce_partials(acc, amax, D.nq, D.partials, D.results, D.ticket, G.tiles)) run_control<T>(D);
+}
+
+// One launch runs a whole Algorithm 1 run (until the control block says done).
+// Every iteration executes the axis passes over all tiles (CTAs loop over
+// tiles) separated by bounded grid barriers; then EVERY CTA folds the last
+// pass's tile partials in the same fixed order and runs the step-size control
+// on its own shared-memory copy of the control block, so all CTAs hold
+// bit-identical state without a third barrier.  CTA 0 writes the state back.
+// The slot pointers and the twiddle tables stay in shared memory for the whole
+// launch.  Must be launched cooperatively (all CTAs co-resident).
+template <typename T, bool CPLX, int EPI>
+__global__ void __launch_bounds__(NTHREADS) k_alg1_persist(PersistArgs<T> P) {
+  using C = typename C2t<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_off[MAXLB];
+  __shared__ T s_rc[MAXLB];
+  __shared__ Alg1Ctl s_ctl;
+  __shared__ void* s_xs[3];
+  __shared__ void* s_gs[3];
+  __shared__ double s_res[NQ];
+  using A = typename AccT<T>::type;
+  // twiddle tables of all axes at the front of dynamic shared memory
+  C* s_tw[3] = {nullptr, nullptr, nullptr};
+  {
+    C* tp = reinterpret_cast<C*>(smem_raw);
+    for (int a = 0; a < P.dim; ++a) {
+      s_tw[a] = tp;
+      for (int i = threadIdx.x; i < P.G[a].F; i += blockDim.x) tp[i] = P.G[a].tw[i];
+      tp += P.G[a].F;
+    }
+  }
+  unsigned char* work = smem_raw + P.tw_bytes;
+  if (threadIdx.x == 0) {
+    s_ctl = *P.D.ctl;
+    for (int i = 0; i < 3; ++i) {
+      s_xs[i] = P.D.xs[i];
+      s_gs[i] = P.D.gs[i];
+    }
+  }
+  __syncthreads();
+  PassData<T> D0 = P.D;
+  D0.ctl = &s_ctl;
+  D0.xs = s_xs;
+  D0.gs = s_gs;
+  auto stamp = [&](int loop, int k) {
+    if (P.dbg && blockIdx.x == 0 && threadIdx.x == 0 && loop < P.dbg_n) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      P.dbg[loop * 4 + k] = t;
+    }
+  };
+  auto writeback = [&]() {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.D.ctl = s_ctl;
+  };
+  for (int loop = 0; loop < P.max_loops; ++loop) {
+    if (s_ctl.done) {
+      writeback();
+      return;
+    }
+    stamp(loop, 0);
+    for (int a = 0; a < P.dim; ++a) {
+      const bool last = a == P.dim - 1;
+      PassData<T> Da = D0;
+      Da.step_on_load = a == 0 ? 1 : 0;
+      Da.acc_in = a > 0 ? P.acc : nullptr;
+      if (!last) {
+        Da.out = P.acc;
+        Da.nq = 0;
+      }
+      for (int blk = blockIdx.x; blk < P.blocks[a]; blk += gridDim.x) {
+        A acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+        T amax = T(0);
+        if (!last) {
+          pass_tile<T, CPLX, EPI_ACC, true>(P.G[a], Da, blk, work, s_off, s_rc, acc, amax, s_tw[a]);
+        } else {
+          pass_tile<T, CPLX, EPI, true>(P.G[a], Da, blk, work, s_off, s_rc, acc, amax, s_tw[a]);
+          block_partial(acc, amax, NQ, P.D.partials + (size_t)blk * NQ);
+        }
+      }
+      if (!grid_barrier(P.bar, P.err)) {
+        writeback();
+        return;
+      }
+      stamp(loop, 1 + (a < 1 ? a : 1));
+    }
+    fold_partials<A>(P.D.partials, P.blocks[P.dim - 1], NQ, s_res);
+    if (threadIdx.x == 0) alg1_control(&s_ctl, s_res);
+    __syncthreads();
+    stamp(loop, 3);
+  }
+  writeback();
 }
 
 // ----------------------------------------------------------------- finite differences
@@ -834,7 +1071,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fd(FDGeom G, const T* __restrict__
   A acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
-  double amax = 0.0;
+  T amax = T(0);
   const long long base = inst * G.M;
   const T a0 = (T)G.ih2[0], a1 = (T)G.ih2[1], a2 = (T)G.ih2[2];
   for (long long li = (long long)tb * blockDim.x + threadIdx.x; li < G.M; li += (long long)G.tiles * blockDim.x) {
@@ -922,7 +1159,7 @@ __global__ void __launch_bounds__(NTHREADS) k_moments(const void* xv, const void
       acc_add(acc[2], tre(gi, gi));
     }
   }
-  reduce_partials(acc, 0.0, 3, partials, results, ticket, tiles);
+  reduce_partials(acc, T(0), 3, partials, results, ticket, tiles);
 }
 
 // out_b = ca[b] * x_b + cb[b] * g_b  (g may be null)
@@ -967,6 +1204,23 @@ static __global__ void k_norm_coef(const double* mom, int nbatch, double h, doub
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbatch) return;
   coef[b] = 1.0 / sqrt(h * mom[(size_t)b * NQ + 0]);
+}
+
+// Shifted subproblem inputs in float32: X^k and P_k = G_k - theta_k X^k
+// (interleaved real components; theta_k is real).
+static __global__ void k_to_shifted_f32(const double* xk, const double* gk, double th, float* xk32, float* pk32,
+                                 long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = xk[i];
+    xk32[i] = (float)x;
+    pk32[i] = (float)(gk[i] - th * x);
+  }
+}
+
+// Z = X^k + D (D from the float32 subproblem), float64.
+static __global__ void k_add_f32_to_f64(const double* xk, const float* d, double* z, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = xk[i] + (double)d[i];
 }
 
 template <typename Ti, typename To>

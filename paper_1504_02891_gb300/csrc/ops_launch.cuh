@@ -165,9 +165,11 @@ void GridDev<T>::destroy() {
   }
 }
 
+// Opt in to `bytes` of dynamic shared memory (static shared memory counts
+// against the 48 KiB default too, so the opt-in is requested for any size).
 template <typename K>
-static void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T, bool CPLX, int EPI>
@@ -176,10 +178,10 @@ static gpe_status launch_pass_t(const PassGeom<T>& G, int blocks, const PassData
   const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
   const int nst = 1 + ((D.xsub || D.step_on_load) ? 1 : 0) + (D.acc_in ? 1 : 0);
   const size_t smem = (size_t)G.F * sizeof(C) + 2 * (size_t)G.LC * G.P * sizeof(C) +
-                      (size_t)nst * G.LB * G.len * vsz;
+                      (size_t)nst * G.LB * G.len * vsz + (EPI != EPI_ACC ? (size_t)G.LB * G.len * sizeof(T) : 0);
   static size_t allowed = 0;
   if (smem > allowed) {
-    allow_smem(k_pass<T, CPLX, EPI>, smem);
+    GPE_CUDA(allow_smem(k_pass<T, CPLX, EPI>, smem));
     allowed = smem;
   }
   ProfScope ps(kernel_name("pass", sizeof(T) == 8, CPLX, EPI, G.M * (blocks / G.tiles)), st);
@@ -317,12 +319,12 @@ gpe_status launch_prolong(const GridHost& gc, const GridHost& gf, const GridDev<
       const int Ff = gf.F[a];
       if (gc.is_complex) {
         static size_t allowed_c = 0;
-        if (smem > allowed_c) { allow_smem(k_prolong_axis<T, true>, smem); allowed_c = smem; }
+        if (smem > allowed_c) { GPE_CUDA(allow_smem(k_prolong_axis<T, true>, smem)); allowed_c = smem; }
         k_prolong_axis<T, true><<<blocks, NTHREADS, smem, st>>>(G, Ff, ilog2(Ff), df.tw[a], gf.ext[a], stride_f,
                                                                 ostride_f, Mf, src, dst);
       } else {
         static size_t allowed_r = 0;
-        if (smem > allowed_r) { allow_smem(k_prolong_axis<T, false>, smem); allowed_r = smem; }
+        if (smem > allowed_r) { GPE_CUDA(allow_smem(k_prolong_axis<T, false>, smem)); allowed_r = smem; }
         k_prolong_axis<T, false><<<blocks, NTHREADS, smem, st>>>(G, Ff, ilog2(Ff), df.tw[a], gf.ext[a], stride_f,
                                                                  ostride_f, Mf, src, dst);
       }
@@ -362,6 +364,75 @@ gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int e
   return GPE_OK;
 }
 
+// Launch shape of the persistent Algorithm 1 kernel: dynamic shared memory for
+// the largest axis pass and as many CTAs as fit co-resident (<= the largest
+// pass's tile count).  grid = 0 if the grid is not spectral.
+template <typename T>
+gpe_status persist_config(const GridHost& g, const GridDev<T>& d, int epi, int* grid, size_t* smem_out) {
+  using C = typename C2t<T>::type;
+  *grid = 0;
+  *smem_out = 0;
+  if (g.disc == GPE_FD) return GPE_OK;
+  const size_t vsz = sizeof(T) * (g.is_complex ? 2 : 1);
+  size_t smem = 0, twb = 0;
+  int maxb = 1;
+  for (int a = 0; a < g.dim; ++a) {
+    const PassGeom<T>& G = d.geom[a];
+    const size_t b = (size_t)G.F * sizeof(C) + 2 * (size_t)G.LC * G.P * sizeof(C) + 2 * (size_t)G.LB * G.len * vsz +
+                     (size_t)G.LB * G.len * sizeof(T);
+    smem = std::max(smem, b);
+    twb += (size_t)G.F * sizeof(C);
+    maxb = std::max(maxb, d.blocks[a]);
+  }
+  twb = (twb + 15) & ~(size_t)15;
+  smem += twb;
+  int dev = 0, nsm = 0, occ = 0;
+  GPE_CUDA(cudaGetDevice(&dev));
+  GPE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  GPE_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return GPE_OK;
+  const void* fn = nullptr;
+  if (epi == EPI_F) fn = g.is_complex ? (const void*)k_alg1_persist<T, true, EPI_F> : (const void*)k_alg1_persist<T, false, EPI_F>;
+  else fn = g.is_complex ? (const void*)k_alg1_persist<T, true, EPI_W> : (const void*)k_alg1_persist<T, false, EPI_W>;
+  GPE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NTHREADS, smem));
+  if (occ < 1) return GPE_OK;
+  *grid = std::min(maxb, occ * nsm);
+  *smem_out = smem;
+  return GPE_OK;
+}
+
+template <typename T>
+gpe_status launch_alg1_persist(const GridHost& g, const GridDev<T>& d, const PassData<T>& D, void* acc,
+                               unsigned int* bar, int* err, int max_loops, int epi, int grid, size_t smem,
+                               cudaStream_t st) {
+  PersistArgs<T> P{};
+  for (int a = 0; a < g.dim; ++a) {
+    P.G[a] = d.geom[a];
+    P.blocks[a] = d.blocks[a];
+  }
+  P.dim = g.dim;
+  P.D = D;
+  P.acc = acc;
+  P.bar = bar;
+  P.err = err;
+  P.max_loops = max_loops;
+  size_t twb = 0;
+  for (int a = 0; a < g.dim; ++a) twb += (size_t)d.geom[a].F * sizeof(typename C2t<T>::type);
+  P.tw_bytes = (twb + 15) & ~(size_t)15;
+  P.dbg = persist_debug_buffer(&P.dbg_n);
+  GPE_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), st));
+  GPE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  void* args[] = {&P};
+  const void* fn = nullptr;
+  if (epi == EPI_F) fn = g.is_complex ? (const void*)k_alg1_persist<T, true, EPI_F> : (const void*)k_alg1_persist<T, false, EPI_F>;
+  else fn = g.is_complex ? (const void*)k_alg1_persist<T, true, EPI_W> : (const void*)k_alg1_persist<T, false, EPI_W>;
+  ProfScope ps(kernel_name("persist", sizeof(T) == 8, g.is_complex, epi, g.M), st);
+  GPE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NTHREADS), args, smem, st));
+  return GPE_OK;
+}
+
 #define GPE_INSTANTIATE(T)                                                                                         \
   template struct GridDev<T>;                                                                                      \
   template gpe_status launch_pass<T>(const GridDev<T>&, int, const PassData<T>&, int, int, cudaStream_t);          \
@@ -373,6 +444,9 @@ gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int e
   template gpe_status launch_inject<T>(const GridHost&, const GridHost&, const void*, void*, cudaStream_t);         \
   template gpe_status launch_prolong<T>(const GridHost&, const GridHost&, const GridDev<T>&, const GridDev<T>&,     \
                                         const void*, void*, void*, void*, cudaStream_t);                           \
-  template gpe_status apply_op<T>(const GridHost&, const GridDev<T>&, PassData<T>, int, void*, bool, cudaStream_t);
+  template gpe_status apply_op<T>(const GridHost&, const GridDev<T>&, PassData<T>, int, void*, bool, cudaStream_t); \
+  template gpe_status persist_config<T>(const GridHost&, const GridDev<T>&, int, int*, size_t*);                      \
+  template gpe_status launch_alg1_persist<T>(const GridHost&, const GridDev<T>&, const PassData<T>&, void*,         \
+                                             unsigned int*, int*, int, int, int, size_t, cudaStream_t);
 
 }  // namespace gpe

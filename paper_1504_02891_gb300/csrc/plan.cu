@@ -460,5 +460,7 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->switch_rel = 1e-6;
   o->chunk = 16;
   o->use_graphs = 1;
+  o->persistent = 1;
+  o->cluster = 1;
   return GPE_OK;
 }

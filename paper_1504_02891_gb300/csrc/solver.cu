@@ -14,6 +14,7 @@
 #include <string.h>
 #include <chrono>
 #include <memory>
+#include <type_traits>
 #include <vector>
 #include "gpe_internal.h"
 
@@ -40,6 +41,14 @@ struct Level {
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};   // objective F, W
   size_t chunk_nodes[2] = {0, 0};
   int chunk_len = 0;
+  // persistent Algorithm 1 launch (spectral grids): barrier words, error flag,
+  // launch shape per objective (grid 0 = not available)
+  unsigned int* bar = nullptr;
+  int* err = nullptr;
+  int* h_err = nullptr;
+  int p_grid[2] = {-1, -1};
+  size_t p_smem[2] = {0, 0};
+  float* d_omega = nullptr;   // Omega as float32 for the cluster engine
 
   gpe_status create(const GridHost& gh) {
     g = gh;
@@ -62,6 +71,14 @@ struct Level {
     GPE_CUDA(cudaMemcpy(d_gs, gs, sizeof(void*) * 3, cudaMemcpyHostToDevice));
     GPE_CUDA(cudaMalloc(&ctl, sizeof(Alg1Ctl)));
     GPE_CUDA(cudaMalloc(&rn, sizeof(RNCtl)));
+    GPE_CUDA(cudaMalloc(&bar, 2 * sizeof(unsigned int)));
+    {
+      const float om = (float)g.omega;
+      GPE_CUDA(cudaMalloc(&d_omega, sizeof(float)));
+      GPE_CUDA(cudaMemcpy(d_omega, &om, sizeof(float), cudaMemcpyHostToDevice));
+    }
+    GPE_CUDA(cudaMalloc(&err, sizeof(int)));
+    GPE_CUDA(cudaMallocHost(&h_err, sizeof(int)));
     GPE_CUDA(cudaMallocHost(&h_ctl, sizeof(Alg1Ctl)));
     GPE_CUDA(cudaMallocHost(&h_rn, sizeof(RNCtl)));
     memset(h_ctl, 0, sizeof(Alg1Ctl));
@@ -84,6 +101,10 @@ struct Level {
     cudaFree(d_gs);
     cudaFree(ctl);
     cudaFree(rn);
+    cudaFree(bar);
+    cudaFree(err);
+    cudaFree(d_omega);
+    cudaFreeHost(h_err);
     cudaFreeHost(h_ctl);
     cudaFreeHost(h_rn);
   }
@@ -116,13 +137,67 @@ static bool trace_on() {
   return on == 1;
 }
 
+static unsigned long long* g_pdbg = nullptr;
+static unsigned long long* g_pdbg_h = nullptr;
+static const int PDBG_N = 256;
+
+unsigned long long* persist_debug_buffer(int* n) {
+  const char* e = getenv("GPE_PERSIST_TRACE");
+  *n = 0;
+  if (!(e && e[0] && e[0] != '0')) return nullptr;
+  if (!g_pdbg) {
+    if (cudaMalloc(&g_pdbg, sizeof(unsigned long long) * 4 * PDBG_N) != cudaSuccess) return nullptr;
+    if (cudaMallocHost(&g_pdbg_h, sizeof(unsigned long long) * 4 * PDBG_N) != cudaSuccess) return nullptr;
+  }
+  cudaMemset(g_pdbg, 0, sizeof(unsigned long long) * 4 * PDBG_N);
+  *n = PDBG_N;
+  return g_pdbg;
+}
+
+void persist_debug_report(cudaStream_t st, long long M, int f64) {
+  if (!g_pdbg) return;
+  cudaMemcpyAsync(g_pdbg_h, g_pdbg, sizeof(unsigned long long) * 4 * PDBG_N, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  double s[3] = {0, 0, 0};
+  int n = 0;
+  for (int i = 0; i < PDBG_N; ++i) {
+    const unsigned long long* t = g_pdbg_h + 4 * i;
+    if (!t[0] || !t[3]) break;
+    s[0] += (double)(t[1] - t[0]);
+    s[1] += (double)(t[2] - t[1]);
+    s[2] += (double)(t[3] - t[2]);
+    ++n;
+  }
+  if (n)
+    fprintf(stderr, "[gpe] persist %s M=%lld loops=%d  pass0 %.2f us  pass1 %.2f us  fold+control %.2f us\n",
+            f64 ? "f64" : "f32", M, n, s[0] / n / 1e3, s[1] / n / 1e3, s[2] / n / 1e3);
+}
+
+static void cluster_debug_report(cudaStream_t st, int nloops) {
+  if (!g_pdbg) return;
+  cudaMemcpyAsync(g_pdbg_h, g_pdbg, sizeof(unsigned long long) * 4 * PDBG_N, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  int n = 0;
+  for (int i = 0; i < nloops; ++i) {
+    const unsigned long long* t = g_pdbg_h + 8 * i;
+    if (!t[0] || !t[7]) break;
+    for (int k = 0; k < 7; ++k) s[k] += (double)(t[k + 1] - t[k]);
+    ++n;
+  }
+  if (n)
+    fprintf(stderr, "[gpe] cluster phases (us, %d loops): step %.2f  x %.2f  sync %.2f  y %.2f  sync %.2f  epi %.2f  "
+            "sync+fold+ctl %.2f\n", n, s[0] / n / 1e3, s[1] / n / 1e3, s[2] / n / 1e3, s[3] / n / 1e3, s[4] / n / 1e3,
+            s[5] / n / 1e3, s[6] / n / 1e3);
+}
+
 struct RunStats {
   int iters = 0, nfe = 0, status = 0;
   double F = 0, res = 0, theta = 0;
 };
 
 struct SolveParams {
-  int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs;
+  int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs, persistent, cluster;
   double eps0, delta_stop, res_tol_X, delta0, switch_rel;
 };
 
@@ -213,6 +288,23 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
   long long launched = 0;
   s = read_ctl<T>(L, st);
   if (s != GPE_OK) return s;
+  if (!L.h_ctl->done && P.persistent && !prof_enabled()) {
+    if (L.p_grid[objective] < 0) {
+      s = persist_config<T>(L.g, L.d, objective == 1 ? EPI_W : EPI_F, &L.p_grid[objective], &L.p_smem[objective]);
+      if (s != GPE_OK) return s;
+    }
+    if (L.p_grid[objective] > 0) {
+      s = launch_alg1_persist<T>(L.g, L.d, L.solver_data(objective), L.acc, L.bar, L.err, (int)max_launch,
+                                 objective == 1 ? EPI_W : EPI_F, L.p_grid[objective], L.p_smem[objective], st);
+      if (s != GPE_OK) return s;
+      GPE_CUDA(cudaMemcpyAsync(L.h_err, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      persist_debug_report(st, L.M, sizeof(T) == 8);
+      s = read_ctl<T>(L, st);
+      if (s != GPE_OK) return s;
+      if (*L.h_err) return fail(GPE_ETIMEOUT, "a grid barrier wait of the persistent Algorithm 1 launch expired");
+      launched = max_launch;
+    }
+  }
   while (!L.h_ctl->done && launched < max_launch) {
     s = run_chunk<T>(L, objective, P, st);
     if (s != GPE_OK) return s;
@@ -234,17 +326,34 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
   return GPE_OK;
 }
 
+// X in xs[slot] scaled to unit 2-norm.
+template <typename T>
+static gpe_status normalise_slot(Level<T>& L, int slot, cudaStream_t st) {
+  gpe_status s = launch_moments<T>(L.xs[slot], nullptr, L.M, 1, L.g.is_complex, L.sc, st);
+  if (s != GPE_OK) return s;
+  s = launch_norm_coef(L.sc.results, 1, 1.0, L.sc.coef, st);
+  if (s != GPE_OK) return s;
+  return launch_axpby<T>(L.xs[slot], nullptr, L.sc.coef, 1, L.M, 1, L.xs[slot], L.g.is_complex, st);
+}
+template <typename T>
+static gpe_status normalise_slot0(Level<T>& L, cudaStream_t st) {
+  return normalise_slot<T>(L, 0, st);
+}
+
 struct LevelStats {
-  int outer = 0, inner = 0, nfe = 0;
+  int outer = 0, inner = 0, inner32 = 0, nfe = 0;
   double F = 0, res = 0, theta = 0;
   bool converged = false;
 };
 
 // Algorithm 2 on one level, starting from xs[0]; result in xk/gk.
 // mode_f32: stop on the float32 criteria (relative residual or stagnation).
+static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double thk, double delta, double sub_tol,
+                                  cudaStream_t st, RunStats& out, bool* used);
+
 template <typename T>
 static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool stop_f32, cudaStream_t st,
-                         LevelStats& ls, double theta_start) {
+                         LevelStats& ls, double theta_start, Level<float>* Lf32 = nullptr) {
   RunStats r;
   const double res_tol = P.res_tol_X;
   // warm start (Algorithm 1, <= k_init iterations; k_init = 0 is one evaluation)
@@ -263,13 +372,38 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
     if (res_tol > 0.0 && resk <= res_tol) { ls.converged = true; break; }
     if (stop_f32 && resk <= P.switch_rel * fabs(thk)) break;
     // subproblem (Eq. tr-sub) by Algorithm 1 on W^(k) from X^k
-    GPE_CUDA(cudaMemcpyAsync(L.xs[0], L.xk, L.bytes, cudaMemcpyDeviceToDevice, st));
     const double sub_tol = fmax(1e-2 * resk, 1e-14);
-    s = alg1_run<T>(L, 1, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r, 0.0, thk);
-    if (s != GPE_OK) return s;
-    ls.inner += r.iters;
-    ls.nfe += r.nfe;
-    const int zc = L.h_ctl->cur;
+    int zc = 0;
+    bool done32 = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (Lf32) {
+        // float32 inner solve in difference form around the float64 outer iterate
+        const long long nreal = L.M * (L.g.is_complex ? 2 : 1);
+        s = launch_to_shifted_f32((const double*)L.xk, (const double*)L.gk, thk, (float*)Lf32->xk,
+                                  (float*)Lf32->gk, nreal, st);
+        if (s != GPE_OK) return s;
+        s = sub_run_cluster(*Lf32, P, thk, delta, sub_tol, st, r, &done32);
+        if (s != GPE_OK) return s;
+        if (done32) {
+          s = launch_add_f32_to_f64((const double*)L.xk, (const float*)Lf32->xs[0], (double*)L.xs[1], nreal, st);
+          if (s != GPE_OK) return s;
+          // Z = X^k + D back on the unit sphere in float64 (D carries float32 rounding)
+          s = normalise_slot<T>(L, 1, st);
+          if (s != GPE_OK) return s;
+          zc = 1;
+          ls.inner32 += r.iters;
+          ls.nfe += r.nfe;
+        }
+      }
+    }
+    if (!done32) {
+      GPE_CUDA(cudaMemcpyAsync(L.xs[0], L.xk, L.bytes, cudaMemcpyDeviceToDevice, st));
+      s = alg1_run<T>(L, 1, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r, 0.0, thk);
+      if (s != GPE_OK) return s;
+      ls.inner += r.iters;
+      ls.nfe += r.nfe;
+      zc = L.h_ctl->cur;
+    }
     // ratio test (Eq. TR-ratio) and delta update (Eq. tau-up)
     RNCtl& rc = *L.h_rn;
     memset(&rc, 0, sizeof(rc));
@@ -369,15 +503,166 @@ static gpe_status fg_run(Level<T>& L, const SolveParams& P, bool stop_f32, cudaS
   return GPE_OK;
 }
 
-// X in xs[0] scaled to unit 2-norm.
-template <typename T>
-static gpe_status normalise_slot0(Level<T>& L, cudaStream_t st) {
-  gpe_status s = launch_moments<T>(L.xs[0], nullptr, L.M, 1, L.g.is_complex, L.sc, st);
+// Algorithm 1 on F in float32 by the cluster engine (2D Fourier grids whose
+// state fits in one cluster's shared memory); the start point is xs[0].
+// Returns false in *used if the grid is not eligible.
+static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool stop_f32, cudaStream_t st,
+                                 LevelStats& ls, double theta_start, bool* used) {
+  *used = false;
+  const GridHost& g = L.g;
+  if (!P.cluster || g.disc != GPE_FOURIER || g.dim != 2 || prof_enabled()) return GPE_OK;
+  int cs, lch, P0, P1;
+  size_t smem;
+  unsigned int vb, vp;
+  if (!cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
+  Alg1Ctl& c = *L.h_ctl;
+  memset(&c, 0, sizeof(c));
+  c.alpha = g.beta / (2.0 * g.hvol);
+  c.rho1 = 1e-4;
+  c.eta = 0.85;
+  c.delta_bt = 0.1;
+  c.eps0 = stop_f32 ? 0.0 : P.eps0;
+  c.res_tol = P.res_tol_X;
+  c.res_rel = stop_f32 ? P.switch_rel : 0.0;
+  c.tau0 = 1e-3;
+  c.renorm_tol = 1e-14;
+  c.max_bt = 10;
+  c.max_iter = P.max_iter;
+  c.objective = 0;
+  c.always_renorm = 1;
+  c.cur = 1;
+  c.trial = 0;
+  c.theta_hint = theta_start;
+  c.stall_iters = stop_f32 ? 40 : 0;
+  c.two_slots = 1;
+  GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
+  ClusterArgs A{};
+  A.n0 = g.ext[0];
+  A.n1 = g.ext[1];
+  A.ninst = 1;
+  A.max_loops = (P.max_iter + 1) * (c.max_bt + 1) + 1;
+  A.dlam0 = (float)(2.0 * M_PI / (g.hi[0] - g.lo[0]));
+  A.dlam1 = (float)(2.0 * M_PI / (g.hi[1] - g.lo[1]));
+  A.V = L.d.V;
+  A.vstride = 0;
+  A.xn = L.d.coord[0];
+  A.yn = L.d.coord[1];
+  A.omega = g.omega != 0.0 ? L.d_omega : nullptr;
+  A.tw0 = L.d.tw[0];
+  A.tw1 = L.d.tw[1];
+  A.x = L.xs[0];
+  A.g = L.gs[0];
+  A.ctl = L.ctl;
+  A.results = L.sc.results;
+  A.dbg = persist_debug_buffer(&A.dbg_n);
+  if (A.dbg) A.dbg_n = A.dbg_n / 2;     // 8 stamps per loop in a buffer of 4 x n
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (trace_on()) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
-  s = launch_norm_coef(L.sc.results, 1, 1.0, L.sc.coef, st);
+  if (A.dbg) cluster_debug_report(st, A.dbg_n);
+  float ms = 0.f;
+  if (e0) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  GPE_CUDA(cudaMemcpyAsync(L.xk, L.xs[0], L.bytes, cudaMemcpyDeviceToDevice, st));
+  GPE_CUDA(cudaMemcpyAsync(L.gk, L.gs[0], L.bytes, cudaMemcpyDeviceToDevice, st));
+  s = read_ctl<float>(L, st);
   if (s != GPE_OK) return s;
-  return launch_axpby<T>(L.xs[0], nullptr, L.sc.coef, 1, L.M, 1, L.xs[0], L.g.is_complex, st);
+  const Alg1Ctl& h = *L.h_ctl;
+  if (trace_on())
+    fprintf(stderr, "[gpe] cluster f32 M=%lld cs=%d iters=%d nfe=%d status=%d F=%.15g res=%.3e  %.3f ms (%.2f us/trial)\n",
+            L.M, cs, h.k, h.nfe, h.status, h.F_cur, h.res, ms, 1e3 * ms / (h.nfe > 0 ? h.nfe : 1));
+  if (h.status == GPE_ENONFINITE) return fail(GPE_ENONFINITE, "non-finite energy during Algorithm 1");
+  ls.inner += h.k;
+  ls.nfe += h.nfe;
+  ls.F = h.F_cur;
+  ls.res = h.res;
+  ls.theta = h.theta_c;
+  ls.converged = (h.status == 0);
+  *used = true;
+  return GPE_OK;
 }
+
+// The regularized Newton subproblem in float32 by the cluster engine, shifted
+// difference form: X^k and P_k = G_k - theta_k X^k already in Lf.xk / Lf.gk
+// (float32).  Result D in Lf.xs[0].  *used = false if not eligible.
+static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double thk, double delta, double sub_tol,
+                                  cudaStream_t st, RunStats& out, bool* used) {
+  *used = false;
+  const GridHost& g = Lf.g;
+  if (!P.cluster || g.disc != GPE_FOURIER || g.dim != 2 || prof_enabled()) return GPE_OK;
+  int cs, lch, P0, P1;
+  size_t smem;
+  unsigned int vb, vp;
+  if (!cluster_shape(g.ext[0], g.ext[1], g.is_complex, 7, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
+  Alg1Ctl& c = *Lf.h_ctl;
+  memset(&c, 0, sizeof(c));
+  c.alpha = g.beta / (2.0 * g.hvol);
+  c.delta = delta;
+  c.theta_ref = thk;
+  c.rho1 = 1e-4;
+  c.eta = 0.85;
+  c.delta_bt = 0.1;
+  c.eps0 = 0.0;
+  c.res_tol = sub_tol;
+  c.tau0 = 1e-3;
+  c.renorm_tol = 1e300;    // the Cayley step keeps the norm; no rescaling in difference form
+  c.max_bt = 10;
+  c.max_iter = P.k_sub;
+  c.objective = 1;
+  c.always_renorm = 0;
+  c.cur = 1;
+  c.trial = 0;
+  c.theta_hint = 0.0;
+  c.two_slots = 1;
+  c.stall_iters = 40;      // float32 floor of the subproblem
+  GPE_CUDA(cudaMemcpyAsync(Lf.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
+  ClusterArgs A{};
+  A.n0 = g.ext[0];
+  A.n1 = g.ext[1];
+  A.ninst = 1;
+  A.max_loops = (P.k_sub + 1) * (c.max_bt + 1) + 1;
+  A.dlam0 = (float)(2.0 * M_PI / (g.hi[0] - g.lo[0]));
+  A.dlam1 = (float)(2.0 * M_PI / (g.hi[1] - g.lo[1]));
+  A.V = Lf.d.V;
+  A.vstride = 0;
+  A.xn = Lf.d.coord[0];
+  A.yn = Lf.d.coord[1];
+  A.omega = g.omega != 0.0 ? Lf.d_omega : nullptr;
+  A.tw0 = Lf.d.tw[0];
+  A.tw1 = Lf.d.tw[1];
+  A.x = Lf.xs[0];
+  A.g = Lf.gs[0];
+  A.ctl = Lf.ctl;
+  A.results = Lf.sc.results;
+  A.shifted = 1;
+  A.xk = Lf.xk;
+  A.pk = Lf.gk;
+  gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
+  if (s != GPE_OK) return s;
+  s = read_ctl<float>(Lf, st);
+  if (s != GPE_OK) return s;
+  const Alg1Ctl& h = *Lf.h_ctl;
+  if (h.status == GPE_ENONFINITE) return fail(GPE_ENONFINITE, "non-finite model value in the subproblem");
+  out.iters = h.k;
+  out.nfe = h.nfe;
+  out.status = h.status;
+  out.F = h.F_cur;
+  out.res = h.res;
+  out.theta = h.theta_c;
+  *used = true;
+  return GPE_OK;
+}
+
 
 template <typename Ti, typename To>
 static gpe_status convert_vec(const void* in, void* out, long long n_real, double scale, cudaStream_t st) {
@@ -456,8 +741,17 @@ static gpe_status solve_levels(std::vector<std::unique_ptr<Level<T>>>& lv, const
     LevelStats ls;
     // float32 bulk of the mixed schedule: Algorithm 1 down to the float32
     // floor on every level (the regularized Newton steps run in float64)
-    gpe_status s = (P.method == 1 || f32) ? fg_run<T>(*lv[l], P, f32, st, ls, theta)
-                                          : rn_run<T>(*lv[l], P, P.k_init, f32, st, ls, theta);
+    gpe_status s = GPE_OK;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (P.method == 1 || f32) {
+        s = fg_run_cluster(*lv[l], P, f32, st, ls, theta, &done);
+        if (s != GPE_OK) return s;
+      }
+    }
+    if (!done)
+      s = (P.method == 1 || f32) ? fg_run<T>(*lv[l], P, f32, st, ls, theta)
+                                 : rn_run<T>(*lv[l], P, P.k_init, f32, st, ls, theta);
     if (s != GPE_OK) return s;
     theta = ls.theta;
     nfe_total += ls.nfe;
@@ -513,6 +807,8 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
   P.method = o.method;
   P.chunk = o.chunk;
   P.use_graphs = o.use_graphs;
+  P.persistent = o.persistent;
+  P.cluster = o.cluster;
   P.eps0 = o.eps0;
   P.delta_stop = o.delta_stop;
   P.res_tol_X = 2.0 * o.res_tol;     // ||A(X)X||_2 = 2 ||H psi - mu psi||_h
@@ -555,9 +851,12 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
     LevelStats ls;
     if (o.mode == 1) {
       SolveParams P64 = P;
-      s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta);
+      // float64 outer iterations; their subproblems in float32 (difference
+      // form) where the cluster engine takes the grid
+      s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta, &Lf);
       rep.outer_f64 = ls.outer;
       rep.inner_f64 = ls.inner;
+      rep.inner_f32 += ls.inner32;
     } else {
       SolveParams P64 = P;
       P64.max_outer = 0;
