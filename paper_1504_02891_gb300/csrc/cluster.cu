@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
           acc_add(acc[Q_VV], tre(vv, vv));
           acc_add(acc[Q_VY], tre(vv, x));
           acc_add(acc[Q_SY], tre(sv, x));
+          acc_add(acc[Q_DF], tre(sv, q) - 0.5f * tre(sv, vv));   // W quadratic: trapezoid exact
           amax = fmaxf(amax, s2);
         }
       } else {

@@ -24,7 +24,7 @@ template <> struct C2t<double> { using type = double2; };
 
 constexpr int NTHREADS = 256;  // largest block size
 constexpr int MAXLB = 128;     // data lines per tile
-constexpr int NQ = 14;         // reduction slots per launch and instance
+constexpr int NQ = 15;         // reduction slots per launch and instance
 
 // Reduction slots of the solver's evaluation passes (EPI_F / EPI_W).
 enum {
@@ -41,7 +41,8 @@ enum {
   Q_VY = 10,   // Re sum conj(v) y
   Q_SY = 11,   // Re sum conj(s) y
   Q_WX = 12,   // W objective: non-quadratic part of W^(k)
-  Q_MAX = 13   // max |s_j| (max-reduction)
+  Q_DF = 13,   // objective(y) - objective(x_c) in difference form
+  Q_MAX = 14   // max |s_j| (max-reduction)
 };
 // Slots of the ratio pass (EPI_RATIO), d = Z - X^k.
 enum { R_AXD = 0, R_DAD = 1, R_QD = 2, R_X2D2 = 3, R_R2 = 4, R_DD = 5, R_GD = 6 };
@@ -64,7 +65,7 @@ struct Alg1Ctl {
                        // (the projected-gradient norm is formed relative to it)
   // iteration state
   int k, m, nfe, accepted_last;
-  double tau, C, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;
+  double tau, Cg, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;   // Cg = C - F_cur
   double a, b, s;      // Cayley step coefficients of the next trial
   double am1;          // a - 1 without cancellation (shifted subproblem form)
   double theta_ref;    // shifted form: theta_k of the outer iterate

@@ -1,0 +1,554 @@
+// lines2d.cuh -- the operator on 2D Fourier grids as two kernels, one per axis,
+// with every line FFT held in registers.
+//
+// A line of F = 2^LF points is owned by F/8 threads, 8 points each: thread j
+// holds the points j + s F/8 (s = 0..7).  The transform is a Stockham autosort
+// FFT of radix-8 stages and, when LF is not a multiple of 3, one radix-4 or
+// radix-2 tail stage; every stage reads the points j + s F/8, so the natural
+// order of the input (coalesced global loads), of the spectrum (symbol
+// multiply) and of the output (coalesced stores) is the register order, and
+// shared memory is touched only by the exchanges between stages (two
+// alternating buffers, one barrier per exchange).  Twiddles are per thread and
+// per stage, computed once per launch.
+//
+//   y-kernel: lines are columns (complex columns; real fields pack two real
+//     columns into one complex line); an optional Cayley step on load
+//     (Theorem 3.3) writes the trial point; output T_y X into the accumulator.
+//   x-kernel: lines are rows (real fields: two rows per complex line); the
+//     epilogue adds the y-kernel's T_y X and V X and runs the pointwise
+//     epilogue of the pass kernels (gradient, Hessian-vector, Algorithm 1 and
+//     ratio-test sums), then the deterministic reduction and control.
+//
+// Spectral operator of both kernels: the x-line symbol lambda_p^2/2 + Omega y
+// lambda_p and the y-line symbol eta_q^2/2 - Omega x eta_q (Eq. fftp36 /
+// Eq. energy-discrete-FP with the rotation term folded per line), 1/F folded
+// into the coefficients, the inverse transform taken as a conjugated forward
+// transform.
+#pragma once
+#include <stdlib.h>
+#include "ops_launch.cuh"
+
+namespace gpe {
+
+constexpr int LINES_THREADS = 256;
+
+template <typename T, int LF>
+struct LineFFT {
+  using C = typename C2t<T>::type;
+  static constexpr int F = 1 << LF;
+  static constexpr int TPL = F / 8;                 // threads per line
+  static constexpr int N8 = LF / 3;                 // radix-8 stages
+  static constexpr int TAIL = LF % 3;               // 1: radix-2 tail stage, 2: radix-4 tail stage
+  // line pitch of the exchange buffers (complex): room for pidx(F - 1), and
+  // = 8 (mod 16) so that neighbouring lines start half a bank row apart
+  static constexpr int P = ((F + F / 16 + 15) & ~15) + 8;
+  // twiddles e^{-2 pi i n / F} come from the table tws (shared memory); in
+  // float32 the thread's 13-17 twiddles are also kept in registers
+  static constexpr bool TW_REG = sizeof(T) == 4;
+  C w8[TW_REG && N8 > 1 ? N8 - 1 : 1][7];
+  C wt[TW_REG ? 6 : 1];
+  const C* tws;
+  int j;
+
+  // twiddle r of radix-8 stage st (>= 1): e^{-2 pi i r k / (8 Ns)}, k = j mod Ns
+  __device__ __forceinline__ C tw8(int st, int r) const {
+    if constexpr (TW_REG) return w8[st - 1][r - 1];
+    const int Ns = 1 << (3 * st);
+    return tws[(r * (j & (Ns - 1))) << (LF - 3 - 3 * st)];
+  }
+  // tail twiddles: radix-4 (i = r - 1 for butterfly j, r + 2 for j + F/8),
+  // radix-2 (i = u)
+  __device__ __forceinline__ C twt(int i) const {
+    if constexpr (TW_REG) return wt[i];
+    if constexpr (TAIL == 2) return tws[i < 3 ? (i + 1) * j : (i - 2) * (j + TPL)];
+    return tws[j + i * TPL];
+  }
+
+  __device__ __forceinline__ void init(int jj, const C* table) {
+    j = jj;
+    tws = table;
+    if constexpr (TW_REG) {
+#pragma unroll
+      for (int st = 1; st < N8; ++st) {
+        const int Ns = 1 << (3 * st);
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) w8[st - 1][r - 1] = table[(r * k) << (LF - 3 - 3 * st)];
+      }
+      if constexpr (TAIL == 2) {
+#pragma unroll
+        for (int r = 1; r < 4; ++r) {
+          wt[r - 1] = table[r * j];
+          wt[r + 2] = table[r * (j + TPL)];
+        }
+      } else if constexpr (TAIL == 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wt[u] = table[j + u * TPL];
+      }
+    }
+  }
+
+  // Forward DFT (unnormalised) of this thread's line: v[s] = x[j + s F/8] in,
+  // X[j + s F/8] out.  ex(par, m) is the shared-memory slot of point m of this
+  // line in exchange buffer par; par alternates between the two buffers.
+  template <typename Ex>
+  __device__ __forceinline__ void forward(C (&v)[8], const Ex& ex, int& par) const {
+#pragma unroll
+    for (int st = 0; st < N8; ++st) {
+      if (st > 0) {
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw8(st, r));
+      }
+      dft8(v);
+      if (st + 1 < N8 || TAIL) {
+        const int Ns = 1 << (3 * st);
+        const int k = j & (Ns - 1);
+        const int mb = ((j - k) << 3) + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) *ex(par, mb + r * Ns) = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = *ex(par, j + s * TPL);
+        par ^= 1;
+      }
+    }
+    if constexpr (TAIL == 2) {
+      // butterflies j (slots 0,2,4,6) and j + F/8 (slots 1,3,5,7)
+      v[2] = cmul(v[2], twt(0));
+      v[4] = cmul(v[4], twt(1));
+      v[6] = cmul(v[6], twt(2));
+      v[3] = cmul(v[3], twt(3));
+      v[5] = cmul(v[5], twt(4));
+      v[7] = cmul(v[7], twt(5));
+      dft4(v[0], v[2], v[4], v[6]);
+      dft4(v[1], v[3], v[5], v[7]);
+    } else if constexpr (TAIL == 1) {
+      // butterflies j + u F/8 (slots u, u + 4)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u + 4] = cmul(v[u + 4], twt(u));
+        dft2(v[u], v[u + 4]);
+      }
+    }
+  }
+
+  // T applied to the line: forward DFT, symbol(m) and conjugation, forward DFT,
+  // conjugation (= inverse DFT of the symbol times the spectrum).
+  template <typename Ex, typename Sym>
+  __device__ __forceinline__ void apply(C (&v)[8], const Ex& ex, int& par, Sym sym) const {
+    forward(v, ex, par);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const T sy = sym(j + s * TPL);
+      v[s].x = sy * v[s].x;
+      v[s].y = -sy * v[s].y;
+    }
+    forward(v, ex, par);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[s].y = -v[s].y;
+  }
+};
+
+// Exchange slots of a line stored contiguously (row pitch P, padded index):
+// the x-kernel, where the threads of a warp share a line.
+template <typename C, int P>
+struct ExRow {
+  C* base;          // line row in buffer 0
+  int pstride;      // buffer 1 - buffer 0
+  __device__ __forceinline__ C* operator()(int par, int m) const { return base + par * pstride + pidx(m); }
+};
+
+// Exchange slots of CW lines stored interleaved (point-major, the CW lines of
+// a point side by side): the y-kernel, where a warp holds 32/CW points of CW
+// lines.  The low bits of the point index are XORed with bits 3.. so that the
+// stride-8 scatter of a radix-8 stage spreads over the bank rows.
+template <typename C, int CW>
+struct ExCols {
+  C* base;          // buffer 0 + column
+  int pstride;
+  static constexpr int G = (128 / int(sizeof(C))) / CW;   // points per 128-byte bank row
+  static constexpr int MASK = G > 1 ? (G > 8 ? 7 : G - 1) : 0;
+  __device__ __forceinline__ C* operator()(int par, int m) const {
+    const int ms = m ^ ((m >> 3) & MASK);
+    return base + par * pstride + ms * CW;
+  }
+};
+
+// The line symbol: c2 lam^2 + c1 coord lam, lam = dlam * (m or m - F).
+template <typename T, int F>
+struct LineSym {
+  T c2, c1c, dl;
+  __device__ __forceinline__ T operator()(int m) const {
+    const T lm = dl * (T)(m < (F >> 1) ? m : m - F);
+    return (c2 * lm + c1c) * lm;
+  }
+};
+
+// Threads of the y-kernel's CTA: 512 in float32 (8 columns of 512 points, 64 B
+// row segments), 256 in float64 (register budget).
+template <typename T> __host__ __device__ constexpr int lines_y_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+// Copy of the twiddle table e^{-2 pi i n / F} into shared memory.
+template <typename C>
+__device__ __forceinline__ void load_table(C* dst, const C* src, int F) {
+  for (int i = threadIdx.x; i < F; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// y-kernel: T_y of columns into D.out; groups of CW complex columns, the CTAs
+// stride over the groups of all instances.  The next group's operands are
+// fetched (cp.async, each thread its own 8 points) while this group's
+// transforms run.
+template <typename T, bool CPLX, int LF>
+__global__ void __launch_bounds__(lines_y_threads<T>()) k_lines_y(PassGeom<T> G, PassData<T> D, int colgroups,
+                                                                  int total) {
+  using FFT = LineFFT<T, LF>;
+  using C = typename FFT::C;
+  constexpr int NT = lines_y_threads<T>();
+  constexpr int TPL = FFT::TPL;
+  constexpr int CW = NT / TPL;
+  constexpr int F = FFT::F;
+  if (D.ctl && D.ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  C* xb = tws + F;                            // [2][F][CW], swizzled points
+  C* pf0 = xb + 2 * F * CW;                   // [8][NT]: next group's input
+  C* pf1 = pf0 + 8 * NT;                      // [8][NT]: next group's second operand
+  load_table(tws, G.tw, F);
+  const int tid = threadIdx.x;
+  const int cl = tid & (CW - 1), j = tid / CW;
+  FFT fft;
+  fft.init(j, tws);
+  int par = 0;
+  const int n0c = CPLX ? G.n0 : G.n0 >> 1;    // complex columns per row
+  const C* xin = (const C*)D.x;
+  const C* src1 = (const C*)D.xsub;
+  C* yst = nullptr;
+  T sa = 0, sb = 0;
+  if (D.use_slots) {
+    const Alg1Ctl* c = D.ctl;
+    xin = (const C*)D.xs[c->trial];
+    if (D.step_on_load) {
+      yst = (C*)D.xs[c->trial];
+      xin = (const C*)D.xs[c->cur];
+      src1 = (const C*)D.gs[c->cur];
+      sa = (T)(c->s * c->a);
+      sb = (T)(c->s * c->b);
+    }
+  }
+  C* out = (C*)D.out;
+  LineSym<T, F> sym;
+  sym.c2 = G.c2;
+  sym.dl = G.dlam;
+  ExCols<C, CW> ex{xb + cl, F * CW};
+  auto ebase = [&](int gidx) {
+    const int inst = gidx / colgroups;
+    const int ccol = (gidx - inst * colgroups) * CW + cl;
+    return (long long)inst * (CPLX ? G.M : G.M >> 1) + ccol;
+  };
+  auto fetch = [&](int gidx) {
+    const long long base = ebase(gidx);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const long long e = base + (long long)(j + s * TPL) * n0c;
+      cp_async(pf0 + s * NT + tid, xin + e);
+      if (src1) cp_async(pf1 + s * NT + tid, src1 + e);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (blockIdx.x < total) fetch(blockIdx.x);
+  for (int gidx = blockIdx.x; gidx < total; gidx += gridDim.x) {
+    const long long base = ebase(gidx);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    C v[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      C a = pf0[s * NT + tid];
+      if (src1) {
+        const C b = pf1[s * NT + tid];
+        a = yst ? sa * a + sb * b : a - b;
+        if (yst) yst[base + (long long)(j + s * TPL) * n0c] = a;
+      }
+      v[s] = a;
+    }
+    // every read of the prefetch buffers is done before they are refilled
+    __syncthreads();
+    if (gidx + (int)gridDim.x < total) fetch(gidx + gridDim.x);
+    const int ccol = (int)(base % n0c);
+    sym.c1c = (CPLX && G.rcoord) ? G.c1 * G.rcoord[ccol] : T(0);
+    fft.apply(v, ex, par, sym);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) out[base + (long long)(j + s * TPL) * n0c] = v[s];
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// x-kernel: T_x of rows, + T_y X (D.acc_in) + V X, then the epilogue, the
+// reduction and the control.  CTA `tile` of an instance takes the line groups
+// tile, tile + tiles_per_inst, ...; the next group's input and this group's
+// epilogue operands are fetched with cp.async (each thread its own points)
+// while the transforms run.
+template <typename T, bool CPLX, int EPI, int LF>
+__global__ void __launch_bounds__(LINES_THREADS) k_lines_x(PassGeom<T> G, PassData<T> D, int tiles_per_inst,
+                                                           int groups) {
+  using FFT = LineFFT<T, LF>;
+  using C = typename FFT::C;
+  using V = typename VT<T, CPLX>::V;
+  using A = typename AccT<T>::type;
+  constexpr int NT = LINES_THREADS;
+  constexpr int TPL = FFT::TPL;
+  constexpr int NL = NT / TPL;
+  constexpr int F = FFT::F;
+  constexpr int NV = CPLX ? 8 : 16;           // values per thread and group (real: two rows)
+  if (D.ctl && D.ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  C* xb = tws + F;                            // [2][NL][P]
+  V* xs = reinterpret_cast<V*>(xb + 2 * NL * FFT::P);   // [2][NV][NT] input, double-buffered
+  V* ea = xs + 2 * NV * NT;                   // [NV][NT] T_y X of this group
+  T* ev = reinterpret_cast<T*>(ea + NV * NT); // [NV][NT] potential of this group
+  load_table(tws, G.tw, F);
+  const int tid = threadIdx.x;
+  const int l = tid / TPL, j = tid & (TPL - 1);
+  FFT fft;
+  fft.init(j, tws);
+  int par = 0;
+  const int inst = blockIdx.x / tiles_per_inst;
+  const int tile = blockIdx.x - inst * tiles_per_inst;
+  const V* xin = (const V*)D.x;
+  if (D.use_slots) xin = (const V*)D.xs[D.ctl->trial];
+  const V* xsub = (const V*)D.xsub;
+  const V* accin = (const V*)D.acc_in;
+  EpiCtx<T, CPLX> E;
+  make_ctx<T, CPLX, EPI, false>(E, D);
+  A acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
+  T amax = T(0);
+  const long long ibase = (long long)inst * G.M;
+  const T* Vp = D.V;
+  LineSym<T, F> sym;
+  sym.c2 = G.c2;
+  sym.dl = G.dlam;
+  ExRow<C, FFT::P> ex{xb + l * FFT::P, NL * FFT::P};
+  // element of value q (q = s, or s + 8 for the second row of a real pair)
+  auto gidx = [&](int grp, int q) -> long long {
+    const int line = grp * NL + l;
+    const int row = (CPLX ? line : 2 * line) + (q >> 3);
+    return ibase + (long long)row * G.n0 + j + (q & 7) * TPL;
+  };
+  auto fetch_x = [&](int grp, int b) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) cp_async(xs + (b * NV + q) * NT + tid, xin + gidx(grp, q));
+  };
+  int b = 0;
+  if (tile < groups) {
+    fetch_x(tile, 0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int grp = tile; grp < groups; grp += tiles_per_inst) {
+    // the previous group's reads of ea/ev are done before they are refilled
+    __syncthreads();
+    const bool more = grp + tiles_per_inst < groups;
+    if (more) fetch_x(grp + tiles_per_inst, b ^ 1);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const long long gi = gidx(grp, q);
+      if (accin) cp_async(ea + q * NT + tid, accin + gi);
+      cp_async(ev + q * NT + tid, Vp + (gi - ibase));
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // this group's input (committed one group earlier)
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    C v[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      if constexpr (CPLX) {
+        V a = xs[(b * NV + s) * NT + tid];
+        if (xsub) a = a - xsub[gidx(grp, s)];
+        v[s] = a;
+      } else {
+        T a = xs[(b * NV + s) * NT + tid], c = xs[(b * NV + s + 8) * NT + tid];
+        if (xsub) {
+          a -= xsub[gidx(grp, s)];
+          c -= xsub[gidx(grp, s + 8)];
+        }
+        v[s].x = a;
+        v[s].y = c;
+      }
+    }
+    const int row0 = CPLX ? grp * NL + l : 2 * (grp * NL + l);
+    sym.c1c = (CPLX && G.rcoord) ? G.c1 * G.rcoord[row0] : T(0);
+    fft.apply(v, ex, par, sym);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(0) : "memory");
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const long long gi = gidx(grp, q);
+      V x = xs[(b * NV + q) * NT + tid];
+      if (xsub) x = x - xsub[gi];
+      V kin;
+      if constexpr (CPLX) kin = v[q];
+      else kin = (q < 8) ? v[q].x : v[q - 8].y;
+      if (accin) kin = kin + ea[q * NT + tid];
+      const V lin = kin + ev[q * NT + tid] * x;
+      epilogue_point<T, CPLX, EPI, false>(E, gi, x, lin, acc, amax);
+    }
+    b ^= 1;
+  }
+  if (EPI == EPI_HESS || D.nq == 0) return;
+  if (reduce_partials(acc, amax, D.nq, D.partials, D.results, D.ticket, tiles_per_inst)) run_control<T>(D);
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+template <typename T, bool CPLX, int EPI, int LF0, int LF1>
+static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, int nbatch, void* acc, bool step_first,
+                                   cudaStream_t st) {
+  using C = typename C2t<T>::type;
+  const PassGeom<T>& gx = d.geom[0];
+  const PassGeom<T>& gy = d.geom[1];
+  constexpr int YT = lines_y_threads<T>();
+  constexpr int CW = YT / ((1 << LF1) / 8);
+  constexpr int NL = LINES_THREADS / ((1 << LF0) / 8);
+  const int n0c = CPLX ? gx.n0 : gx.n0 / 2;
+  const int colgroups = n0c / CW;
+  const int lines = CPLX ? gx.n1 : gx.n1 / 2;
+  const int groups = lines / NL;
+  // y pass (first: it also forms the trial point)
+  {
+    PassData<T> Dy = D;
+    Dy.step_on_load = step_first ? 1 : 0;
+    Dy.acc_in = nullptr;
+    Dy.out = acc;
+    Dy.nq = 0;
+    Dy.control = 0;
+    const size_t smem = ((size_t)(1 << LF1) * (1 + 2 * CW) + 16 * (size_t)YT) * sizeof(C);
+    static int occ = -1;
+    if (occ < 0) {
+      GPE_CUDA(cudaFuncSetAttribute(k_lines_y<T, CPLX, LF1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_y<T, CPLX, LF1>, YT, smem));
+      if (occ < 1) occ = 1;
+    }
+    const int total = nbatch * colgroups;
+    const int grid = std::min(total, 4 * occ * num_sms());
+    ProfScope ps(kernel_name("lines_y", sizeof(T) == 8, CPLX, EPI_ACC, gx.M * nbatch), st);
+    k_lines_y<T, CPLX, LF1><<<grid, YT, smem, st>>>(gy, Dy, colgroups, total);
+    GPE_CUDA(cudaGetLastError());
+  }
+  // x pass with the epilogue
+  {
+    PassData<T> Dx = D;
+    Dx.step_on_load = 0;
+    Dx.acc_in = acc;
+    constexpr int NV = CPLX ? 8 : 16;
+    const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
+    const size_t smem = ((size_t)(1 << LF0) + 2 * (size_t)NL * LineFFT<T, LF0>::P) * sizeof(C) +
+                        3 * (size_t)NV * LINES_THREADS * vsz + (size_t)NV * LINES_THREADS * sizeof(T);
+    static int occ = -1;
+    if (occ < 0) {
+      GPE_CUDA(cudaFuncSetAttribute(k_lines_x<T, CPLX, EPI, LF0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_x<T, CPLX, EPI, LF0>, LINES_THREADS, smem));
+      if (occ < 1) occ = 1;
+    }
+    // about four resident waves in all, at most the reduction scratch's capacity
+    const long long want = 4LL * occ * num_sms();
+    int tiles = groups;
+    while (tiles > 1 && (long long)tiles * nbatch > want) tiles = (tiles + 1) / 2;
+    while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
+    if ((long long)tiles * nbatch > d.max_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
+    ProfScope ps(kernel_name("lines_x", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
+    k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, LINES_THREADS, smem, st>>>(gx, Dx, tiles, groups);
+    GPE_CUDA(cudaGetLastError());
+  }
+  return GPE_OK;
+}
+
+// The supported shapes: n0, n1 in {64, ..., 1024}; the column groups and line
+// groups must tile the grid.
+template <typename T>
+static bool lines2d_ok(const GridHost& g) {
+  if (g.disc != GPE_FOURIER || g.dim != 2) return false;
+  const int n0 = g.ext[0], n1 = g.ext[1];
+  auto pow2 = [](int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; };
+  if (!pow2(n0) || !pow2(n1)) return false;
+  const int cw = (sizeof(T) == 4 ? 512 : 256) / (n1 / 8), nl = LINES_THREADS / (n0 / 8);
+  const int n0c = g.is_complex ? n0 : n0 / 2;
+  const int lines = g.is_complex ? n1 : n1 / 2;
+  return n0c % cw == 0 && lines % nl == 0;
+}
+
+template <typename T, bool CPLX, int EPI, int LF0>
+static gpe_status lines2d_dispatch1(const GridDev<T>& d, const PassData<T>& D, int nbatch, void* acc, bool step_first,
+                                    int lf1, cudaStream_t st) {
+  switch (lf1) {
+    case 6: return launch_lines2d_t<T, CPLX, EPI, LF0, 6>(d, D, nbatch, acc, step_first, st);
+    case 7: return launch_lines2d_t<T, CPLX, EPI, LF0, 7>(d, D, nbatch, acc, step_first, st);
+    case 8: return launch_lines2d_t<T, CPLX, EPI, LF0, 8>(d, D, nbatch, acc, step_first, st);
+    case 9: return launch_lines2d_t<T, CPLX, EPI, LF0, 9>(d, D, nbatch, acc, step_first, st);
+    case 10: return launch_lines2d_t<T, CPLX, EPI, LF0, 10>(d, D, nbatch, acc, step_first, st);
+  }
+  return fail(GPE_EINVAL, "unsupported line length");
+}
+
+template <typename T, bool CPLX, int EPI>
+static gpe_status lines2d_dispatch0(const GridDev<T>& d, const PassData<T>& D, int nbatch, void* acc, bool step_first,
+                                    int lf0, int lf1, cudaStream_t st) {
+  switch (lf0) {
+    case 6: return lines2d_dispatch1<T, CPLX, EPI, 6>(d, D, nbatch, acc, step_first, lf1, st);
+    case 7: return lines2d_dispatch1<T, CPLX, EPI, 7>(d, D, nbatch, acc, step_first, lf1, st);
+    case 8: return lines2d_dispatch1<T, CPLX, EPI, 8>(d, D, nbatch, acc, step_first, lf1, st);
+    case 9: return lines2d_dispatch1<T, CPLX, EPI, 9>(d, D, nbatch, acc, step_first, lf1, st);
+    case 10: return lines2d_dispatch1<T, CPLX, EPI, 10>(d, D, nbatch, acc, step_first, lf1, st);
+  }
+  return fail(GPE_EINVAL, "unsupported line length");
+}
+
+// GPE_LINES2D=0 in the environment selects the general axis-pass kernels
+// instead (for comparisons); read once.
+static bool lines2d_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("GPE_LINES2D");
+    on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return on != 0;
+}
+
+template <typename T>
+gpe_status launch_lines2d(const GridHost& g, const GridDev<T>& d, const PassData<T>& D, int epi, void* acc,
+                          bool step_first, cudaStream_t st, bool* handled) {
+  *handled = false;
+  if (!lines2d_ok<T>(g) || !lines2d_enabled()) return GPE_OK;
+  const int lf0 = ilog2(g.ext[0]), lf1 = ilog2(g.ext[1]);
+  const int nb = g.nbatch;
+  gpe_status s;
+#define GPE_L2D_CASE(E)                                                                           \
+  case E:                                                                                         \
+    s = g.is_complex ? lines2d_dispatch0<T, true, E>(d, D, nb, acc, step_first, lf0, lf1, st)     \
+                     : lines2d_dispatch0<T, false, E>(d, D, nb, acc, step_first, lf0, lf1, st);   \
+    break;
+  switch (epi) {
+    GPE_L2D_CASE(EPI_GRAD)
+    GPE_L2D_CASE(EPI_HESS)
+    GPE_L2D_CASE(EPI_F)
+    GPE_L2D_CASE(EPI_W)
+    GPE_L2D_CASE(EPI_RATIO)
+    default:
+      return GPE_OK;
+  }
+#undef GPE_L2D_CASE
+  if (s == GPE_OK) *handled = true;
+  return s;
+}
+
+}  // namespace gpe

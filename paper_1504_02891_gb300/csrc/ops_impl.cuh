@@ -443,6 +443,52 @@ static __device__ void fold_partials(const double* partials, int tiles, int nq, 
   __syncthreads();
 }
 
+// Several instances: warp w folds instances w, w + nwarps, ... (lanes stride
+// over the tiles in a fixed order, then a fixed shuffle tree), so the final
+// fold of a large batch is spread over the CTA's warps.  Ends with a barrier.
+template <typename A>
+static __device__ void fold_partials_warps(const double* partials, int tiles, int nq, double* results, int ninst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const A* pp = reinterpret_cast<const A*>(partials);
+  for (int b = warp; b < ninst; b += nw) {
+    for (int q = 0; q < NQ; ++q) {
+      if (q >= nq && q != Q_MAX) {
+        if (lane == 0) results[(size_t)b * NQ + q] = 0.0;
+        continue;
+      }
+      A x;
+      acc_zero(x);
+      for (int i = lane; i < tiles; i += 32) {
+        const size_t o = ((size_t)b * tiles + i) * NQ + q;
+        if constexpr (std::is_same<A, double>::value) {
+          const double w = __ldcg(pp + o);
+          x = (q == Q_MAX) ? fmax(x, w) : x + w;
+        } else {
+          const float2 f = __ldcg(reinterpret_cast<const float2*>(pp + o));
+          A w;
+          w.hi = f.x;
+          w.lo = f.y;
+          if (q == Q_MAX) df_max(x, w);
+          else acc_merge(x, w);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        if constexpr (std::is_same<A, double>::value) {
+          const double w = __shfl_down_sync(0xffffffffu, x, o);
+          x = (q == Q_MAX) ? fmax(x, w) : x + w;
+        } else {
+          const DF w = shfl_down(x, o);
+          if (q == Q_MAX) df_max(x, w);
+          else acc_merge(x, w);
+        }
+      }
+      if (lane == 0) results[(size_t)b * NQ + q] = acc_value(x);
+    }
+  }
+  __syncthreads();
+}
+
 // Block partial, then the last CTA to finish (atomic ticket) folds all
 // partials per instance into results[inst][q].  Returns true in the last CTA.
 template <typename A, typename M>
@@ -456,8 +502,8 @@ static __device__ bool reduce_partials(A (&acc)[NQ], M amax2, int nq, double* pa
   if (!s_last) return false;
   __threadfence();
   const int ninst = gridDim.x / tiles_per_inst;
-  for (int b = 0; b < ninst; ++b)
-    fold_partials<A>(partials + (size_t)b * tiles_per_inst * NQ, tiles_per_inst, nq, results + (size_t)b * NQ);
+  if (ninst == 1) fold_partials<A>(partials, tiles_per_inst, nq, results);
+  else fold_partials_warps<A>(partials, tiles_per_inst, nq, results, ninst);
   if (threadIdx.x == 0) *ticket = 0u;
   __threadfence();
   __syncthreads();
@@ -534,10 +580,14 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
     c->status = 4;  // GPE_ENONFINITE
     return;
   }
+  // Eq. NMLS-Armijo relative to the current point: with Cg = C - F(X_cur),
+  // F(Y) <= C - rho1 tau res^2 reads dF <= Cg - rho1 tau res^2, dF formed
+  // pointwise (no cancellation of two nearly equal objective values)
+  const double dF = r[Q_DF];
   bool accept = true;
   if (c->phase != 0) {
-    const double thr = c->C - c->rho1 * c->tau * c->res * c->res;
-    accept = (obj <= thr) || (c->m >= c->max_bt);
+    const double thr = c->Cg - c->rho1 * c->tau * c->res * c->res;
+    accept = (dF <= thr) || (c->m >= c->max_bt);
   }
   if (!accept) {
     c->tau *= c->delta_bt;
@@ -578,15 +628,16 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
   c->res = nY * sqrt(PPn);
   c->smax = r[Q_MAX];
   if (c->phase == 0) {
-    c->C = obj;
+    c->Cg = 0.0;
     c->Q = 1.0;
     c->k = 0;
     c->tau = c->tau0;
     c->phase = 1;
     c->has_cur = 1;
   } else {
+    // C+ = (eta Q C + F(Y)) / Q+  =>  C+ - F(Y) = eta Q (Cg - dF) / Q+
     const double Qn = c->eta * c->Q + 1.0;
-    c->C = (c->eta * c->Q * c->C + obj) / Qn;
+    c->Cg = c->eta * c->Q * (c->Cg - dF) / Qn;
     c->Q = Qn;
     c->k += 1;
     c->tau_last = c->tau;
@@ -709,6 +760,13 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     acc_add(acc[Q_VV], tre(v, v));
     acc_add(acc[Q_VY], tre(v, y));
     acc_add(acc[Q_SY], tre(s, y));
+    // objective(y) - objective(x_c) by the trapezoid rule on the theta-shifted
+    // gradients (q + q_c = 2q - v); exact for the quadratic part, the quartic
+    // term of F adds -alpha Re<s, y + x_c> |s|^2.  The dropped real multiple
+    // of y + x_c changes the objective only off the unit sphere.
+    T df = tre(s, q) - T(0.5) * tre(s, v);
+    if (EPI == EPI_F) df -= E.nl * tre(s, y + xc) * s2;
+    acc_add(acc[Q_DF], df);
     amax = fmax(amax, s2);
   } else if (EPI == EPI_RATIO) {
     const V d = x;

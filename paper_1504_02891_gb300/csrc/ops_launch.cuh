@@ -336,9 +336,20 @@ gpe_status launch_prolong(const GridHost& gc, const GridHost& gf, const GridDev<
   return GPE_OK;
 }
 
+// 2D Fourier grids: the register-FFT line kernels (lines2d.cuh); *handled is
+// false for shapes they do not cover.
+template <typename T>
+gpe_status launch_lines2d(const GridHost& g, const GridDev<T>& d, const PassData<T>& D, int epi, void* acc,
+                          bool step_first, cudaStream_t st, bool* handled);
+
 template <typename T>
 gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int epi, void* acc, bool step_first,
                     cudaStream_t st) {
+  if (g.disc == GPE_FOURIER && g.dim == 2) {
+    bool handled = false;
+    gpe_status s = launch_lines2d<T>(g, d, D, epi, acc, step_first, st, &handled);
+    if (s != GPE_OK || handled) return s;
+  }
   if (g.disc == GPE_FD) {
     if (step_first) {
       gpe_status s = launch_step<T>(D.xs, D.gs, D.ctl, g.M * g.nbatch, g.is_complex, st);

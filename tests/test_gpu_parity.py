@@ -247,13 +247,17 @@ def test_algorithm1_float32_tracks_oracle():
     assert abs(rep["E"] - r.F) <= 1e-4 * abs(r.F), (rep["E"], r.F)
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
-def test_persistent_launch_matches_per_iteration_launches(mode):
-    """The persistent Algorithm 1 launch (grid barriers, control in CTA 0)
-    performs the same arithmetic in the same order as one launch per pass:
-    identical iterates and report."""
-    p = W.config("c2")
-    p["n"] = (128, 128)
+@pytest.mark.parametrize("case", ["c2_128_fp64", "c2_128_mixed", "c3_32_fp64"])
+def test_persistent_launch_matches_per_iteration_launches(case):
+    """The persistent Algorithm 1 launch (grid barriers, control in every CTA)
+    runs the same algorithm as one launch per pass: the same iteration counts
+    (up to a step decided differently by rounding) and the same state and
+    energy to float64 rounding.  The per-launch path of 2D Fourier grids uses
+    the register-FFT line kernels, so the two differ in rounding order."""
+    cfg, n, mode = {"c2_128_fp64": ("c2", (128, 128), 0), "c2_128_mixed": ("c2", (128, 128), 1),
+                    "c3_32_fp64": ("c3", (32, 32, 32), 0)}[case]
+    p = W.config(cfg)
+    p["n"] = n
     psi0 = W.gaussian(p)
     outs, reps = [], []
     for persistent in (0, 1):
@@ -261,9 +265,14 @@ def test_persistent_launch_matches_per_iteration_launches(mode):
             t = G.to_device(psi0)
             reps.append(plan.solve(t, mode=mode, levels=2, res_tol=1e-9, persistent=persistent))
             outs.append(host(t))
-    assert np.array_equal(outs[0], outs[1])
-    for k in ("E", "mu", "res", "inner_f32", "inner_f64", "outer_f64", "nfe"):
-        assert reps[0][k] == reps[1][k], k
+    scale = np.abs(outs[0]).max()
+    assert np.abs(outs[0] - outs[1]).max() <= 2e-8 * scale   # both stop near res 1e-9
+    assert abs(reps[0]["E"] - reps[1]["E"]) <= 1e-13 * abs(reps[0]["E"])
+    assert abs(reps[0]["mu"] - reps[1]["mu"]) <= 1e-12 * abs(reps[0]["mu"])
+    for k in ("inner_f32", "inner_f64", "outer_f64"):
+        assert abs(reps[0][k] - reps[1][k]) <= 2, k
+    for r in reps:
+        assert r["status"] == 0
 
 
 @pytest.mark.parametrize("case", ["real128", "rot64", "rot256"])
