@@ -44,6 +44,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the trial point Y); the ratio pass (read Z, X^k, G^k).  Per real number: 4 B
 # (float32) or 8 B (float64); complex doubles it.
 ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3}
+# DRAM bytes (read + write) of one H psi apply of the happly workload, from the
+# ncu capture summarised in profiles/happly_64x512sq_c64_lines.txt (k_lines_y
+# 227.6 MB + k_lines_x 374.0 MB); must be re-taken whenever those kernels change.
+HAPPLY_DRAM_BYTES_PER_APPLY = 601.6e6
 
 
 def parse():
@@ -176,7 +180,7 @@ def roofline_from_profile(prof, peaks):
             continue
         kern, size = name.split("@")
         parts = kern.split("_")             # pass_f32_r_W
-        if parts[0] not in ("pass", "fd", "step"):
+        if parts[0] not in ("pass", "fd", "step", "linesy", "linesx"):
             continue
         key = (parts[1], parts[2], int(size))
         g = groups.setdefault(key, {"ms": 0.0, "final": {}, "kernels": {}})
@@ -231,9 +235,12 @@ def happly_throughput(G, torch, W, peaks, reps=20):
     achieved = alg / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     plan.close()
-    return {"workload": "H psi apply, 64 x 512^2 complex64 rotating (Omega=0.9), float32",
-            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "us_per_apply": ms * 1e3, "alg_bytes_per_apply": alg}
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": HAPPLY_DRAM_BYTES_PER_APPLY,
+            "kernel": "H psi apply = k_lines_y + k_lines_x (register-FFT line kernels), "
+                      "64 x 512^2 complex64 rotating (Omega=0.9), float32",
+            "us_per_apply": ms * 1e3, "alg_bytes_per_apply": alg, "launches_per_apply": 2,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 
 
 def our_arm(args):
@@ -365,7 +372,7 @@ def our_arm(args):
         "throughput": {"value": world * 1e3 / ms_mixed, "unit": "ground states/s"},
         "E": rep["E"], "mu": rep["mu"], "res": rep["res"], "delta_E_rel_vs_oracle": dE,
         "solver": {k: rep[k] for k in ("outer_f32", "outer_f64", "inner_f32", "inner_f64", "nfe", "ms_f32", "ms_f64")},
-        "roofline": roof, "happly": happly,
+        "roofline": happly, "solve_operator_roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},

@@ -440,7 +440,7 @@ static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, in
     }
     const int total = nbatch * colgroups;
     const int grid = std::min(total, 4 * occ * num_sms());
-    ProfScope ps(kernel_name("lines_y", sizeof(T) == 8, CPLX, EPI_ACC, gx.M * nbatch), st);
+    ProfScope ps(kernel_name("linesy", sizeof(T) == 8, CPLX, EPI_ACC, gx.M * nbatch), st);
     k_lines_y<T, CPLX, LF1><<<grid, YT, smem, st>>>(gy, Dy, colgroups, total);
     GPE_CUDA(cudaGetLastError());
   }
@@ -466,7 +466,7 @@ static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, in
     while (tiles > 1 && (long long)tiles * nbatch > want) tiles = (tiles + 1) / 2;
     while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
     if ((long long)tiles * nbatch > d.max_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
-    ProfScope ps(kernel_name("lines_x", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
+    ProfScope ps(kernel_name("linesx", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
     k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, LINES_THREADS, smem, st>>>(gx, Dx, tiles, groups);
     GPE_CUDA(cudaGetLastError());
   }
