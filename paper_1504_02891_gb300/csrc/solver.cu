@@ -624,7 +624,7 @@ static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double
   c.trial = 0;
   c.theta_hint = 0.0;
   c.two_slots = 1;
-  c.stall_iters = 40;      // float32 floor of the subproblem
+  c.stall_iters = 0;       // sub_tol is relative to ||P_k||: above the float32 floor
   GPE_CUDA(cudaMemcpyAsync(Lf.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   ClusterArgs A{};
   A.n0 = g.ext[0];
