@@ -187,6 +187,30 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
 gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
                              gpe_solve_report* report);
 
+/* Many independent ground-state problems in one call: Algorithm 1 (Theorem
+ * 3.3 step, Eq. bb-1 BB step, Eq. NMLS-Armijo search) in float32 with float64
+ * reductions and device-side control for every instance at once -- the
+ * float32 bulk of the mixed schedule, batched.  problems[i] (i < n): 2D
+ * Fourier grids whose state fits one thread-block cluster (n[0], n[1] powers
+ * of two, up to 256^2; real with omega = 0, or complex); each instance has
+ * its own beta, omega and potential.  Instances with the same grid (extents,
+ * box, complexity) run in one cluster launch, clusters taking the next
+ * unstarted instance when one finishes, each instance stopping on its own
+ * criteria.  psi[i]: device buffer of problems[i]'s grid in float32 (complex64
+ * interleaved when complex), the initial guess in physical units on entry
+ * (normalised on the grid), the state on return.  opts (NULL = defaults):
+ * max_iter bounds the iterations per instance; an instance stops when
+ * ||H psi - mu psi||_h <= res_tol, or ||A(X)X|| <= switch_rel |X^*G|, or after
+ * 40 accepted steps without a new smallest residual (the float32 floor).
+ * reports[i] receives E, mu and res of the final evaluation (float64 sums of
+ * float32 values), inner_f32 (iterations), nfe, and status GPE_OK, GPE_ENOCONV
+ * (max_iter reached) or GPE_ENONFINITE.  Runs on cuda_stream (NULL = legacy
+ * default stream) and synchronises; allocates its own scratch per call.
+ * Returns GPE_EINVAL for a grid outside the above and GPE_ENONFINITE if any
+ * instance went non-finite (the other states are still written). */
+gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* const* psi, const gpe_solve_opts* opts,
+                           gpe_solve_report* reports, void* cuda_stream);
+
 /* Allocation-free Cayley step (the paper has no counterpart: this is a
  * packaging variant of gpe_feasible_step for callers that cannot call
  * cudaMalloc -- e.g. code running inside a stream capture that must stay free

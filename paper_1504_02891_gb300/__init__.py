@@ -116,6 +116,8 @@ def load():
         "gpe_prolong": ([vp, vp, vp, vp], ip),
         "gpe_solve_opts_default": ([C.POINTER(SolveOpts)], ip),
         "gpe_rnewton_solve": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveReport)], ip),
+        "gpe_solve_batch": ([C.POINTER(Problem), ip, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(SolveReport),
+                             vp], ip),
         "gpe_kernel_launches": ([], C.c_int64),
         "gpe_profile_enable": ([ip], ip),
         "gpe_profile_summary": ([C.c_char_p, ip], ip),
@@ -270,6 +272,33 @@ class Plan:
         r = SolveReport()
         _check(load().gpe_rnewton_solve(self.handle, _ptr(psi), C.byref(o), C.byref(r)), allow=(5,))
         return r.as_dict()
+
+
+def solve_batch(params_list, psis, stream=None, **opts):
+    """gpe_solve_batch: float32 Algorithm 1 for many independent problems in
+    one call.  params_list[i] is a workload parameter dict (2D Fourier, up to
+    256^2), psis[i] a contiguous CUDA tensor of its grid (complex64 or float32),
+    updated in place.  Returns the reports as a list of dicts."""
+    import torch
+    n = len(params_list)
+    if n != len(psis) or n == 0:
+        raise ValueError("need one psi per problem")
+    probs = (Problem * n)(*[Problem.from_params(p) for p in params_list])
+    for t in psis:
+        if not t.is_cuda or not t.is_contiguous() or t.dtype not in (torch.complex64, torch.float32):
+            raise ValueError("psi tensors must be contiguous CUDA complex64/float32")
+    ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in psis])
+    o = SolveOpts()
+    _check(load().gpe_solve_opts_default(C.byref(o)))
+    for k, v in opts.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    reps = (SolveReport * n)()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().gpe_solve_batch(probs, n, ptrs, C.byref(o), reps, C.c_void_p(stream.cuda_stream)))
+    return [r.as_dict() for r in reps]
 
 
 def kernel_launches():

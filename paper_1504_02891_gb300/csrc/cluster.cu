@@ -83,7 +83,14 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       A.dbg[loop * 8 + k] = t;
     }
   };
-  for (int inst = cid; inst < A.ninst; inst += ncl) {
+  __shared__ int s_inst;
+  for (int it = 0;; ++it) {
+    // the next instance: rank 0 draws it, the cluster reads rank 0's copy
+    if (rank == 0 && tid == 0) s_inst = A.next ? (int)atomicAdd(A.next, 1u) : cid + it * ncl;
+    cl.sync();
+    const int inst = *cl.map_shared_rank(&s_inst, 0);
+    cl.sync();
+    if (inst >= A.ninst) break;
     const long long gbase = (long long)inst * n0 * n1 + (long long)rank * nloc;
     const V* xin = reinterpret_cast<const V*>(A.x) + gbase;
     const float* Vp = A.V + inst * A.vstride + (long long)rank * nloc;

@@ -174,6 +174,8 @@ struct ClusterArgs {
   int shifted;             // 1: regularized Newton subproblem in difference form (see cluster.cu)
   const void* xk;          // shifted: X^k (float32) [ninst][n1][n0]
   const void* pk;          // shifted: P_k = G_k - theta_k X^k (float32)
+  unsigned int* next;      // instance counter (zero at launch): clusters take the next
+                           // unstarted instance when they finish one; null: round robin
 };
 
 // Arguments of the persistent Algorithm 1 kernel.

@@ -503,21 +503,11 @@ static gpe_status fg_run(Level<T>& L, const SolveParams& P, bool stop_f32, cudaS
   return GPE_OK;
 }
 
-// Algorithm 1 on F in float32 by the cluster engine (2D Fourier grids whose
-// state fits in one cluster's shared memory); the start point is xs[0].
-// Returns false in *used if the grid is not eligible.
-static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool stop_f32, cudaStream_t st,
-                                 LevelStats& ls, double theta_start, bool* used) {
-  *used = false;
-  const GridHost& g = L.g;
-  if (!P.cluster || g.disc != GPE_FOURIER || g.dim != 2 || prof_enabled()) return GPE_OK;
-  int cs, lch, P0, P1;
-  size_t smem;
-  unsigned int vb, vp;
-  if (!cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
-  Alg1Ctl& c = *L.h_ctl;
+// Control block of a float32 Algorithm 1 run on F in the cluster engine
+// (readings S3-S5: constants; two slots; the float32 floor ends the run).
+static void init_cluster_ctl(Alg1Ctl& c, double alpha, const SolveParams& P, bool stop_f32, double theta_start) {
   memset(&c, 0, sizeof(c));
-  c.alpha = g.beta / (2.0 * g.hvol);
+  c.alpha = alpha;
   c.rho1 = 1e-4;
   c.eta = 0.85;
   c.delta_bt = 0.1;
@@ -535,6 +525,22 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
   c.theta_hint = theta_start;
   c.stall_iters = stop_f32 ? 40 : 0;
   c.two_slots = 1;
+}
+
+// Algorithm 1 on F in float32 by the cluster engine (2D Fourier grids whose
+// state fits in one cluster's shared memory); the start point is xs[0].
+// Returns false in *used if the grid is not eligible.
+static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool stop_f32, cudaStream_t st,
+                                 LevelStats& ls, double theta_start, bool* used) {
+  *used = false;
+  const GridHost& g = L.g;
+  if (!P.cluster || g.disc != GPE_FOURIER || g.dim != 2 || prof_enabled()) return GPE_OK;
+  int cs, lch, P0, P1;
+  size_t smem;
+  unsigned int vb, vp;
+  if (!cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
+  Alg1Ctl& c = *L.h_ctl;
+  init_cluster_ctl(c, g.beta / (2.0 * g.hvol), P, stop_f32, theta_start);
   GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   ClusterArgs A{};
   A.n0 = g.ext[0];
@@ -912,4 +918,175 @@ extern "C" gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gp
   if (report) *report = rep;
   if (s != GPE_OK) return s;
   return rep.status == GPE_ENOCONV ? GPE_ENOCONV : GPE_OK;
+}
+
+// ----------------------------------------------------------------- batched solves
+namespace gpe {
+
+// Device buffers of one group of same-grid instances.
+struct BatchGroup {
+  std::vector<int> idx;
+  GridHost g;
+  GridDev<float> d;
+  Scratch sc;
+  void* x = nullptr;
+  void* gr = nullptr;
+  float* V = nullptr;
+  float* omega = nullptr;
+  Alg1Ctl* ctl = nullptr;
+  unsigned int* next = nullptr;
+  ~BatchGroup() {
+    d.destroy();
+    sc.destroy();
+    cudaFree(x);
+    cudaFree(gr);
+    cudaFree(V);
+    cudaFree(omega);
+    cudaFree(ctl);
+    cudaFree(next);
+  }
+};
+
+static bool same_grid(const GridHost& a, const GridHost& b) {
+  return a.ext[0] == b.ext[0] && a.ext[1] == b.ext[1] && a.is_complex == b.is_complex && a.lo[0] == b.lo[0] &&
+         a.lo[1] == b.lo[1] && a.hi[0] == b.hi[0] && a.hi[1] == b.hi[1];
+}
+
+static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh, void* const* psi,
+                                  const SolveParams& P, gpe_solve_report* reports, cudaStream_t st) {
+  const int n = (int)B.idx.size();
+  const GridHost& g = B.g;
+  const long long M = g.M;
+  const int cplx = g.is_complex;
+  const long long nreal = M * (cplx ? 2 : 1);
+  const size_t vbytes = sizeof(float) * (size_t)nreal;
+  gpe_status s = B.d.create(g);
+  if (s != GPE_OK) return s;
+  const long long tiles = std::max<long long>(1, std::min<long long>((M + NTHREADS - 1) / NTHREADS, 512));
+  s = B.sc.create((size_t)tiles * n, n);
+  if (s != GPE_OK) return s;
+  GPE_CUDA(cudaMalloc(&B.x, vbytes * n));
+  GPE_CUDA(cudaMalloc(&B.gr, vbytes * n));
+  GPE_CUDA(cudaMalloc(&B.V, sizeof(float) * (size_t)M * n));
+  GPE_CUDA(cudaMalloc(&B.omega, sizeof(float) * n));
+  GPE_CUDA(cudaMalloc(&B.ctl, sizeof(Alg1Ctl) * n));
+  GPE_CUDA(cudaMalloc(&B.next, sizeof(unsigned int)));
+  // per-instance potential, Omega and control (alpha = beta / (2 h_vol))
+  std::vector<float> hv((size_t)M * n), hom(n);
+  std::vector<Alg1Ctl> hc(n);
+  for (int k = 0; k < n; ++k) {
+    const GridHost& gi = gh[B.idx[k]];
+    for (long long i = 0; i < M; ++i) hv[(size_t)k * M + i] = (float)gi.V[i];
+    hom[k] = (float)gi.omega;
+    init_cluster_ctl(hc[k], gi.beta / (2.0 * gi.hvol), P, true, 0.0);
+  }
+  GPE_CUDA(cudaMemcpyAsync(B.V, hv.data(), sizeof(float) * hv.size(), cudaMemcpyHostToDevice, st));
+  GPE_CUDA(cudaMemcpyAsync(B.omega, hom.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+  GPE_CUDA(cudaMemcpyAsync(B.ctl, hc.data(), sizeof(Alg1Ctl) * n, cudaMemcpyHostToDevice, st));
+  GPE_CUDA(cudaMemsetAsync(B.next, 0, sizeof(unsigned int), st));
+  // initial data: psi -> X = sqrt(h_vol) psi, then unit 2-norm per instance
+  const double sh = sqrt(g.hvol);
+  for (int k = 0; k < n; ++k) {
+    s = launch_convert<float, float>((const float*)psi[B.idx[k]], (float*)((char*)B.x + vbytes * k), nreal, sh, st);
+    if (s != GPE_OK) return s;
+  }
+  s = launch_moments<float>(B.x, nullptr, M, n, cplx, B.sc, st);
+  if (s != GPE_OK) return s;
+  s = launch_norm_coef(B.sc.results, n, 1.0, B.sc.coef, st);
+  if (s != GPE_OK) return s;
+  s = launch_axpby<float>(B.x, nullptr, B.sc.coef, 1, M, n, B.x, cplx, st);
+  if (s != GPE_OK) return s;
+  // all instances of the group in one cluster launch
+  ClusterArgs A{};
+  A.n0 = g.ext[0];
+  A.n1 = g.ext[1];
+  A.ninst = n;
+  A.max_loops = (P.max_iter + 1) * (hc[0].max_bt + 1) + 1;
+  A.dlam0 = (float)(2.0 * M_PI / (g.hi[0] - g.lo[0]));
+  A.dlam1 = (float)(2.0 * M_PI / (g.hi[1] - g.lo[1]));
+  A.V = B.V;
+  A.vstride = M;
+  A.xn = B.d.coord[0];
+  A.yn = B.d.coord[1];
+  A.omega = cplx ? B.omega : nullptr;
+  A.tw0 = B.d.tw[0];
+  A.tw1 = B.d.tw[1];
+  A.x = B.x;
+  A.g = B.gr;
+  A.ctl = B.ctl;
+  A.results = B.sc.results;
+  A.next = B.next;
+  s = launch_cluster_alg1(A, cplx, st);
+  if (s != GPE_OK) return s;
+  // results back to psi (physical units) and the reports
+  for (int k = 0; k < n; ++k) {
+    s = launch_convert<float, float>((const float*)((char*)B.x + vbytes * k), (float*)psi[B.idx[k]], nreal, 1.0 / sh,
+                                     st);
+    if (s != GPE_OK) return s;
+  }
+  GPE_CUDA(cudaMemcpyAsync(hc.data(), B.ctl, sizeof(Alg1Ctl) * n, cudaMemcpyDeviceToHost, st));
+  GPE_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < n; ++k) {
+    const Alg1Ctl& c = hc[k];
+    gpe_solve_report& r = reports[B.idx[k]];
+    memset(&r, 0, sizeof(r));
+    r.E = c.F_cur;
+    r.mu = 0.5 * c.theta_c;
+    r.res = 0.5 * c.res;
+    r.status = c.status == 4 ? GPE_ENONFINITE : (c.status == 5 ? GPE_ENOCONV : GPE_OK);
+    r.inner_f32 = c.k;
+    r.nfe = c.nfe;
+  }
+  return GPE_OK;
+}
+
+}  // namespace gpe
+
+extern "C" gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* const* psi,
+                                      const gpe_solve_opts* opts, gpe_solve_report* reports, void* cuda_stream) {
+  if (!problems || !psi || !reports || n < 1) return fail(GPE_EINVAL, "NULL argument or n < 1");
+  gpe_solve_opts o;
+  if (opts) o = *opts;
+  else gpe_solve_opts_default(&o);
+  if (o.max_iter < 1 || !(o.res_tol >= 0)) return fail(GPE_EINVAL, "invalid solve options");
+  std::vector<GridHost> gh(n);
+  for (int i = 0; i < n; ++i) {
+    if (!psi[i]) return fail(GPE_EINVAL, "psi[i] is NULL");
+    gpe_status s = grid_from_problem(&problems[i], 1, gh[i]);
+    if (s != GPE_OK) return s;
+    const GridHost& g = gh[i];
+    int cs, lch, P0, P1;
+    size_t smem;
+    unsigned int vb, vp;
+    if (g.disc != GPE_FOURIER || g.dim != 2 ||
+        !cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp))
+      return fail(GPE_EINVAL, "gpe_solve_batch takes 2D Fourier grids whose state fits one cluster (<= 256^2)");
+  }
+  SolveParams P{};
+  P.max_iter = o.max_iter;
+  P.eps0 = o.eps0;
+  P.res_tol_X = 2.0 * o.res_tol;
+  P.switch_rel = o.switch_rel;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // group the instances by grid; one cluster launch per group
+  std::vector<std::unique_ptr<BatchGroup>> groups;
+  for (int i = 0; i < n; ++i) {
+    BatchGroup* grp = nullptr;
+    for (auto& b : groups)
+      if (same_grid(b->g, gh[i])) grp = b.get();
+    if (!grp) {
+      groups.emplace_back(new BatchGroup());
+      grp = groups.back().get();
+      grp->g = gh[i];
+      grp->g.nbatch = 1;
+    }
+    grp->idx.push_back(i);
+  }
+  for (auto& b : groups) {
+    gpe_status s = run_batch_group(*b, gh, psi, P, reports, st);
+    if (s != GPE_OK) return s;
+  }
+  for (int i = 0; i < n; ++i)
+    if (reports[i].status == GPE_ENONFINITE) return fail(GPE_ENONFINITE, "non-finite energy in a batched instance");
+  return GPE_OK;
 }

@@ -60,3 +60,26 @@ def test_invalid_problem_rejected_without_device():
         st = L.gpe_plan_create(ctypes.byref(pr), 1, G.F64, None, ctypes.byref(h))
         assert st == 1, (p, st)
         assert len(L.gpe_last_error()) > 0
+
+
+def test_batch_rejects_unsupported_grids_without_device():
+    """gpe_solve_batch validates every problem on the host before any CUDA
+    call: a 3D grid, a sine grid and a grid too large for one cluster."""
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1504_02891_gb300 import build as B
+    B.build()
+    import paper_1504_02891_gb300 as G
+    import workloads as W
+    L = G.load()
+    for p in (W.problem(3, (32, 32, 32), (-1,) * 3, (1,) * 3, "fourier"),
+              W.problem(2, (64, 64), (-1, -1), (1, 1), "sine"),
+              W.problem(2, (1024, 1024), (-1, -1), (1, 1), "fourier", omega=0.5, is_complex=True)):
+        probs = (G.Problem * 1)(G.Problem.from_params(p))
+        dummy = ctypes.c_void_p(16)
+        ptrs = (ctypes.c_void_p * 1)(dummy)
+        reps = (G.SolveReport * 1)()
+        st = L.gpe_solve_batch(probs, 1, ptrs, None, reps, None)
+        assert st == 1, (p["dim"], p["disc"], st)
+        assert len(L.gpe_last_error()) > 0

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "problem", "axis_nodes", "array_shape", "cell_volume", "normalise",
-    "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep", "random_field",
+    "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep", "sweep_initial", "random_field",
 ]
 
 
@@ -183,6 +183,12 @@ def batched_sweep(count=256, seed=20150410):
                            beta=beta, omega=om, is_complex=True,
                            potential={"kind": "harmonic", "gamma": (1.0, gy)}))
     return out
+
+
+def sweep_initial(p, i):
+    """Initial data of batched-sweep instance i: phi_c with seeded phase noise
+    of amplitude 1e-2 (as config 4), noise seed 1504 + i."""
+    return rotating_initial(p, "c", noise=1e-2, seed=1504 + i)
 
 
 def random_field(p, seed=0, smooth=0.0):
