@@ -77,7 +77,8 @@ gpe_status launch_pass(const GridDev<T>& d, int axis, const PassData<T>& D, int 
 template <typename T>
 gpe_status launch_fd(const GridDev<T>& d, const PassData<T>& D, int cplx, int epi, cudaStream_t st);
 template <typename T>
-gpe_status launch_step(void* const* xs, void* const* gs, const Alg1Ctl* ctl, long long n, int cplx, cudaStream_t st);
+gpe_status launch_step(void* const* xs, void* const* gs, const Alg1Ctl* ctl, long long n, int cplx, cudaStream_t st,
+                       const void* xk = nullptr);
 template <typename T>
 gpe_status launch_moments(const void* x, const void* g, long long M, int nbatch, int cplx, Scratch& sc,
                           cudaStream_t st);

@@ -47,7 +47,9 @@ enum {
 // Slots of the ratio pass (EPI_RATIO), d = Z - X^k.
 enum { R_AXD = 0, R_DAD = 1, R_QD = 2, R_X2D2 = 3, R_R2 = 4, R_DD = 5, R_GD = 6 };
 
-enum Epi { EPI_ACC = 0, EPI_GRAD = 1, EPI_HESS = 2, EPI_F = 3, EPI_W = 4, EPI_RATIO = 5 };
+// EPI_WS: the regularized Newton model in difference form (unknown D = X - X^k,
+// gradient G^ = P_k + H_k D + (delta - theta_k) D; base = X^k, gk = P_k).
+enum Epi { EPI_ACC = 0, EPI_GRAD = 1, EPI_HESS = 2, EPI_F = 3, EPI_W = 4, EPI_RATIO = 5, EPI_WS = 6 };
 
 // Device-resident state of one Algorithm 1 run (one instance).  The passes read
 // the slot indices and scalars at their start; the last CTA of the final pass

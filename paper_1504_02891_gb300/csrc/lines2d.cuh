@@ -543,6 +543,7 @@ gpe_status launch_lines2d(const GridHost& g, const GridDev<T>& d, const PassData
     GPE_L2D_CASE(EPI_F)
     GPE_L2D_CASE(EPI_W)
     GPE_L2D_CASE(EPI_RATIO)
+    GPE_L2D_CASE(EPI_WS)
     default:
       return GPE_OK;
   }

@@ -707,7 +707,7 @@ struct EpiCtx {
   const V* gc;
   const V* base;
   const V* gk;
-  T nl, shift, lin_scale, th_c, delta;
+  T nl, shift, lin_scale, th_c, delta, thk;
 };
 
 template <typename T, bool CPLX, int EPI, bool COH = false, typename A>
@@ -768,6 +768,37 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
     if (EPI == EPI_F) df -= E.nl * tre(s, y + xc) * s2;
     acc_add(acc[Q_DF], df);
     amax = fmax(amax, s2);
+  } else if (EPI == EPI_WS) {
+    // difference form (the unknown y is D = X - X^k): G^ = P_k + H_k D +
+    // (delta - theta_k) D, objective Re<P_k, D> + theta_k Re<X^k, D> +
+    // 1/2 Re<D, H_k D> + delta/2 |D|^2, moments of X = X^k + D
+    const V y = x;
+    const V xk = ldv<COH>(E.base + gi);
+    const V pk = ldv<COH>(E.gk + gi);
+    const T x2 = tre(xk, xk), R = tre(xk, y);
+    const V hD = E.lin_scale * lin + (T(4) * E.nl) * (x2 * y + (T(2) * R) * xk);
+    const V gh = pk + hD + (E.delta - E.thk) * y;
+    E.out[gi] = gh;
+    const V X = xk + y;
+    acc_add(acc[Q_WX], tre(pk, y) + E.thk * R + T(0.5) * tre(y, hD) + T(0.5) * E.delta * tre(y, y));
+    acc_add(acc[Q_NY], tre(X, X));
+    acc_add(acc[Q_YG], tre(X, gh));
+    acc_add(acc[Q_GG], tre(gh, gh));
+    const V q = gh - E.th_c * X;
+    acc_add(acc[Q_Q], tre(q, q));
+    acc_add(acc[Q_QY], tre(q, X));
+    const V yc = E.xc ? ldv<COH>(E.xc + gi) : vzero<V>();
+    const V gc = E.gc ? ldv<COH>(E.gc + gi) : vzero<V>();
+    const V s = y - yc;
+    const V v = (gh - gc) - E.th_c * s;
+    const T s2 = tre(s, s);
+    acc_add(acc[Q_SS], s2);
+    acc_add(acc[Q_SV], tre(s, v));
+    acc_add(acc[Q_VV], tre(v, v));
+    acc_add(acc[Q_VY], tre(v, X));
+    acc_add(acc[Q_SY], tre(s, X));
+    acc_add(acc[Q_DF], tre(s, q) - T(0.5) * tre(s, v));   // the model is quadratic: trapezoid exact
+    amax = fmax(amax, s2);
   } else if (EPI == EPI_RATIO) {
     const V d = x;
     const V xk = ldv<COH>(E.base + gi);
@@ -815,6 +846,7 @@ __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& 
       }
     }
   }
+  E.thk = D.ctl ? (T)rdc<COH>(D.ctl->theta_ref) : T(0);
   if (D.rn) E.nl = (T)D.rn->alpha;
 }
 
@@ -1183,13 +1215,21 @@ __global__ void __launch_bounds__(NTHREADS) k_fd(FDGeom G, const T* __restrict__
 // Cayley step of Theorem 3.3 into the trial slot (FD path; the spectral path
 // forms it while loading the first pass).
 template <typename T, bool CPLX>
-__global__ void k_step(void* const* xs, void* const* gs, const Alg1Ctl* c, long long n) {
+__global__ void k_step(void* const* xs, void* const* gs, const Alg1Ctl* c, long long n, const void* xkv) {
   using V = typename VT<T, CPLX>::V;
   if (c->done) return;
   const V* X = (const V*)xs[c->cur];
   const V* Gv = (const V*)gs[c->cur];
   V* Y = (V*)xs[c->trial];
   const T a = (T)(c->s * c->a), b = (T)(c->s * c->b);
+  if (xkv) {
+    // difference form: D+ = (a - 1) X^k + a D + b G^ (no renormalisation)
+    const V* xk = (const V*)xkv;
+    const T am1 = (T)c->am1, a1 = (T)c->a, b1 = (T)c->b;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      Y[i] = am1 * xk[i] + a1 * X[i] + b1 * Gv[i];
+    return;
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     Y[i] = a * X[i] + b * Gv[i];
 }

@@ -204,6 +204,7 @@ gpe_status launch_pass(const GridDev<T>& d, int axis, const PassData<T>& D, int 
     GPE_PASS_CASE(EPI_F)
     GPE_PASS_CASE(EPI_W)
     GPE_PASS_CASE(EPI_RATIO)
+    GPE_PASS_CASE(EPI_WS)
   }
 #undef GPE_PASS_CASE
   return fail(GPE_EINVAL, "unknown epilogue");
@@ -238,10 +239,11 @@ static inline int ew_blocks(long long n) {
 }
 
 template <typename T>
-gpe_status launch_step(void* const* xs, void* const* gs, const Alg1Ctl* ctl, long long n, int cplx, cudaStream_t st) {
+gpe_status launch_step(void* const* xs, void* const* gs, const Alg1Ctl* ctl, long long n, int cplx, cudaStream_t st,
+                       const void* xk) {
   ProfScope ps(kernel_name("step", sizeof(T) == 8, cplx, -1, n), st);
-  if (cplx) k_step<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n);
-  else k_step<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n);
+  if (cplx) k_step<T, true><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n, xk);
+  else k_step<T, false><<<ew_blocks(n), NTHREADS, 0, st>>>(xs, gs, ctl, n, xk);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
 }
@@ -352,7 +354,7 @@ gpe_status apply_op(const GridHost& g, const GridDev<T>& d, PassData<T> D, int e
   }
   if (g.disc == GPE_FD) {
     if (step_first) {
-      gpe_status s = launch_step<T>(D.xs, D.gs, D.ctl, g.M * g.nbatch, g.is_complex, st);
+      gpe_status s = launch_step<T>(D.xs, D.gs, D.ctl, g.M * g.nbatch, g.is_complex, st, nullptr);
       if (s != GPE_OK) return s;
     }
     return launch_fd<T>(d, D, g.is_complex, epi, st);
@@ -448,7 +450,8 @@ gpe_status launch_alg1_persist(const GridHost& g, const GridDev<T>& d, const Pas
   template struct GridDev<T>;                                                                                      \
   template gpe_status launch_pass<T>(const GridDev<T>&, int, const PassData<T>&, int, int, cudaStream_t);          \
   template gpe_status launch_fd<T>(const GridDev<T>&, const PassData<T>&, int, int, cudaStream_t);                  \
-  template gpe_status launch_step<T>(void* const*, void* const*, const Alg1Ctl*, long long, int, cudaStream_t);     \
+  template gpe_status launch_step<T>(void* const*, void* const*, const Alg1Ctl*, long long, int, cudaStream_t,      \
+                                     const void*);                                                                 \
   template gpe_status launch_moments<T>(const void*, const void*, long long, int, int, Scratch&, cudaStream_t);     \
   template gpe_status launch_axpby<T>(const void*, const void*, const double*, int, long long, int, void*, int,     \
                                       cudaStream_t);                                                               \

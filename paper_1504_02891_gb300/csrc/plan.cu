@@ -64,11 +64,11 @@ ProfScope::~ProfScope() {
 }
 
 const char* kernel_name(const char* base, int f64, int cplx, int epi, long long points) {
-  static const char* epis[] = {"acc", "grad", "hess", "F", "W", "ratio"};
+  static const char* epis[] = {"acc", "grad", "hess", "F", "W", "ratio", "WS"};
   static std::mutex mu;
   static std::map<std::string, std::string> names;
   std::string k = std::string(base) + (f64 ? "_f64" : "_f32") + (cplx ? "_c" : "_r");
-  if (epi >= 0 && epi < 6) k += std::string("_") + epis[epi];
+  if (epi >= 0 && epi < 7) k += std::string("_") + epis[epi];
   if (points >= 0) k += "@" + std::to_string(points);
   std::lock_guard<std::mutex> lk(mu);
   auto it = names.find(k);

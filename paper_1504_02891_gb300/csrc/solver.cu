@@ -38,8 +38,8 @@ struct Level {
   RNCtl* rn = nullptr;
   Alg1Ctl* h_ctl = nullptr;
   RNCtl* h_rn = nullptr;
-  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};   // objective F, W
-  size_t chunk_nodes[2] = {0, 0};
+  cudaGraphExec_t chunk_exec[3] = {nullptr, nullptr, nullptr};   // objective F, W, W difference form
+  size_t chunk_nodes[3] = {0, 0, 0};
   int chunk_len = 0;
   // persistent Algorithm 1 launch (spectral grids): barrier words, error flag,
   // launch shape per objective (grid 0 = not available)
@@ -86,7 +86,7 @@ struct Level {
     return GPE_OK;
   }
   void destroy() {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
       if (chunk_exec[i]) cudaGraphExecDestroy(chunk_exec[i]);
     d.destroy();
     sc.destroy();
@@ -116,7 +116,8 @@ struct Level {
     D.use_slots = 1;
     D.V = d.V;
     D.lin_scale = 2.0;
-    D.base = objective == 1 ? xk : nullptr;
+    D.base = objective >= 1 ? xk : nullptr;   // W: X^k; difference form: X^k (and gk = P_k)
+    D.gk = objective == 2 ? gk : nullptr;
     D.partials = sc.partials;
     D.results = sc.results;
     D.ticket = sc.ticket;
@@ -208,14 +209,26 @@ static gpe_status read_ctl(Level<T>& L, cudaStream_t st) {
   return GPE_OK;
 }
 
+// Epilogue of an Algorithm 1 objective: 0 F, 1 W^(k), 2 W^(k) in difference form.
+static int objective_epi(int objective) { return objective == 0 ? EPI_F : (objective == 1 ? EPI_W : EPI_WS); }
+
 // Queue `n` Algorithm 1 iterations (each: Cayley step formed on load, the
 // operator passes, control in the last CTA).
 template <typename T>
 static gpe_status queue_iters(Level<T>& L, int objective, int n, cudaStream_t st) {
   const PassData<T> D = L.solver_data(objective);
-  const int epi = objective == 1 ? EPI_W : EPI_F;
+  const int epi = objective_epi(objective);
+  const long long n_all = L.M * L.g.nbatch;   // elements (complex or real)
   for (int i = 0; i < n; ++i) {
-    gpe_status s = apply_op<T>(L.g, L.d, D, epi, L.acc, true, st);
+    gpe_status s;
+    if (objective == 2) {
+      // difference form: the step needs X^k, so it runs as its own kernel
+      s = launch_step<T>(D.xs, D.gs, D.ctl, n_all, L.g.is_complex, st, L.xk);
+      if (s != GPE_OK) return s;
+      s = apply_op<T>(L.g, L.d, D, epi, L.acc, false, st);
+    } else {
+      s = apply_op<T>(L.g, L.d, D, epi, L.acc, true, st);
+    }
     if (s != GPE_OK) return s;
   }
   return GPE_OK;
@@ -254,7 +267,7 @@ static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cu
 template <typename T>
 static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_iter, double res_tol, double eps0,
                            double delta, const SolveParams& P, cudaStream_t st, RunStats& out, double res_rel = 0.0,
-                           double theta_hint = 0.0, int stall_iters = 0) {
+                           double theta_hint = 0.0, int stall_iters = 0, double theta_ref = 0.0) {
   Alg1Ctl& c = *L.h_ctl;
   memset(&c, 0, sizeof(c));
   c.alpha = L.g.beta / (2.0 * L.g.hvol);
@@ -279,16 +292,22 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
   c.phase = 0;
   c.theta_hint = theta_hint;
   c.stall_iters = stall_iters;
+  if (objective == 2) {
+    // difference form: the Cayley curve keeps ||X^k + D||, no rescaling
+    c.always_renorm = 0;
+    c.renorm_tol = 1e300;
+    c.theta_ref = theta_ref;
+  }
   GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   // first evaluation (no step)
-  gpe_status s = apply_op<T>(L.g, L.d, L.solver_data(objective), objective == 1 ? EPI_W : EPI_F, L.acc, false, st);
+  gpe_status s = apply_op<T>(L.g, L.d, L.solver_data(objective), objective_epi(objective), L.acc, false, st);
   if (s != GPE_OK) return s;
   // bounded: every queued iteration either accepts or backtracks (<= max_bt times)
   const long long max_launch = (long long)(max_iter + 1) * (c.max_bt + 1) + 1;
   long long launched = 0;
   s = read_ctl<T>(L, st);
   if (s != GPE_OK) return s;
-  if (!L.h_ctl->done && P.persistent && !prof_enabled()) {
+  if (!L.h_ctl->done && P.persistent && objective < 2 && !prof_enabled()) {
     if (L.p_grid[objective] < 0) {
       s = persist_config<T>(L.g, L.d, objective == 1 ? EPI_W : EPI_F, &L.p_grid[objective], &L.p_smem[objective]);
       if (s != GPE_OK) return s;
@@ -384,8 +403,19 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
         if (s != GPE_OK) return s;
         s = sub_run_cluster(*Lf32, P, thk, delta, sub_tol, st, r, &done32);
         if (s != GPE_OK) return s;
+        int dslot = 0;
+        if (!done32 && L.g.disc != GPE_FD) {
+          // grids the cluster does not hold: the same difference form with the
+          // per-launch passes (D = 0 at the start)
+          GPE_CUDA(cudaMemsetAsync(Lf32->xs[0], 0, Lf32->bytes, st));
+          s = alg1_run<float>(*Lf32, 2, 0, P.k_sub, sub_tol, 0.0, delta, P, st, r, 0.0, 0.0, 0, thk);
+          if (s != GPE_OK) return s;
+          dslot = Lf32->h_ctl->cur;
+          done32 = true;
+        }
         if (done32) {
-          s = launch_add_f32_to_f64((const double*)L.xk, (const float*)Lf32->xs[0], (double*)L.xs[1], nreal, st);
+          s = launch_add_f32_to_f64((const double*)L.xk, (const float*)Lf32->xs[dslot], (double*)L.xs[1], nreal,
+                                    st);
           if (s != GPE_OK) return s;
           // Z = X^k + D back on the unit sphere in float64 (D carries float32 rounding)
           s = normalise_slot<T>(L, 1, st);
@@ -766,6 +796,76 @@ static gpe_status solve_levels(std::vector<std::unique_ptr<Level<T>>>& lv, const
   return GPE_OK;
 }
 
+// Mixed schedule (mode 1), level by level of the cascade: float32 Algorithm 1
+// from the prolonged state to the float32 floor; then, on the finest level and
+// on any level where the float32 run stopped short of switch_rel (stagnation,
+// as in rotating problems), Algorithm 2 with float64 outer quantities and
+// float32 subproblems in difference form.  A level that ended in float64 is
+// prolonged in float64.  Result in C.ld.back()->xk.
+static gpe_status solve_mixed(SolverCache& C, const SolveParams& P, cudaStream_t st, LevelStats& fs, int& nfe,
+                              gpe_solve_report& rep) {
+  double theta = 0.0;
+  bool prev_double = false;
+  double ms32 = 0.0, ms64 = 0.0;
+  for (size_t l = 0; l < C.lf.size(); ++l) {
+    Level<float>& Lf = *C.lf[l];
+    Level<double>& Ld = *C.ld[l];
+    const long long nreal = Lf.M * (Lf.g.is_complex ? 2 : 1);
+    const bool fine = l + 1 == C.lf.size();
+    gpe_status s = GPE_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    if (l > 0) {
+      if (prev_double) {
+        s = prolong_into<double>(*C.ld[l - 1], Ld, st);
+        if (s == GPE_OK) s = convert_vec<double, float>(Ld.xs[0], Lf.xs[0], nreal, 1.0, st);
+        if (s == GPE_OK) s = normalise_slot0<float>(Lf, st);
+      } else {
+        s = prolong_into<float>(*C.lf[l - 1], Lf, st);
+      }
+      if (s != GPE_OK) return s;
+    }
+    LevelStats ls;
+    bool done = false;
+    s = fg_run_cluster(Lf, P, true, st, ls, theta, &done);
+    if (s != GPE_OK) return s;
+    if (!done) s = fg_run<float>(Lf, P, true, st, ls, theta);
+    if (s != GPE_OK) return s;
+    nfe += ls.nfe;
+    theta = ls.theta;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    auto t1 = std::chrono::steady_clock::now();
+    ms32 += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (fine) {
+      rep.inner_f32 = ls.inner;
+      rep.outer_f32 = 0;
+    }
+    const bool at_floor = ls.res <= P.switch_rel * fabs(ls.theta);
+    prev_double = false;
+    if (!fine && at_floor) continue;
+    if (P.method == 1 && !fine) continue;
+    s = convert_vec<float, double>(Lf.xk, Ld.xs[0], nreal, 1.0, st);
+    if (s == GPE_OK) s = normalise_slot0<double>(Ld, st);
+    if (s != GPE_OK) return s;
+    LevelStats l2;
+    s = rn_run<double>(Ld, P, 0, false, st, l2, theta, &Lf);
+    if (s != GPE_OK) return s;
+    nfe += l2.nfe;
+    theta = l2.theta;
+    prev_double = true;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    ms64 += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    if (fine) {
+      fs = l2;
+      rep.outer_f64 = l2.outer;
+      rep.inner_f64 = l2.inner;
+      rep.inner_f32 += l2.inner32;
+    }
+  }
+  rep.ms_f32 = ms32;
+  rep.ms_f64 = ms64;
+  return GPE_OK;
+}
+
 template <typename Tp>
 static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, gpe_solve_report& rep) {
   auto t0 = std::chrono::steady_clock::now();
@@ -782,9 +882,9 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
     GPE_CUDA(cudaStreamCreateWithFlags(&C->st, cudaStreamNonBlocking));
     GPE_CUDA(cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming));
     gpe_status s = GPE_OK;
-    if (o.mode == 0) s = make_levels<double>(plan->g, o.levels, C->ld);
-    else s = make_levels<float>(plan->g, o.levels, C->lf);
-    if (s == GPE_OK && o.mode != 0) {
+    if (o.mode != 2) s = make_levels<double>(plan->g, o.levels, C->ld);
+    if (s == GPE_OK && o.mode != 0) s = make_levels<float>(plan->g, o.levels, C->lf);
+    if (s == GPE_OK && o.mode == 2) {
       GridHost g = plan->g;
       g.nbatch = 1;
       C->fine64.reset(new Level<double>());
@@ -836,6 +936,12 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
     rep.inner_f64 = fs.inner;
     GPE_CUDA(cudaStreamSynchronize(st));
     rep.ms_f64 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  } else if (o.mode == 1) {
+    s = load_initial<Tp, float>(plan, *C, *C->lf[0], psi, inject);
+    if (s != GPE_OK) return s;
+    s = solve_mixed(*C, P, st, fs, nfe, rep);
+    if (s != GPE_OK) return s;
+    fin = C->ld.back().get();
   } else {
     s = load_initial<Tp, float>(plan, *C, *C->lf[0], psi, inject);
     if (s != GPE_OK) return s;
@@ -855,15 +961,8 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
     s = normalise_slot0<double>(*fin, st);
     if (s != GPE_OK) return s;
     LevelStats ls;
-    if (o.mode == 1) {
-      SolveParams P64 = P;
-      // float64 outer iterations; their subproblems in float32 (difference
-      // form) where the cluster engine takes the grid
-      s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta, &Lf);
-      rep.outer_f64 = ls.outer;
-      rep.inner_f64 = ls.inner;
-      rep.inner_f32 += ls.inner32;
-    } else {
+    {
+      // mode 2: one float64 evaluation of the float32 result
       SolveParams P64 = P;
       P64.max_outer = 0;
       s = rn_run<double>(*fin, P64, 0, false, st, ls, fs.theta);
