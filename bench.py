@@ -68,6 +68,20 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(values, world):
+    """Element-wise maximum of per-rank values (the slowest rank's step
+    times); the identity at world = 1.  Works on any initialised process
+    group (NCCL on the GPU machine, gloo in the CPU tests)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 # --------------------------------------------------------------------------- oracle legs
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -340,13 +354,7 @@ def our_arm(args):
     barrier()
     clk = clocks.stop(gpu_index=local)
 
-    ms_mixed = statistics.mean(t_mixed)
-    ms_fp64 = statistics.mean(t_fp64)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_mixed, ms_fp64], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fp64 = float(tt[0]), float(tt[1])
+    ms_mixed, ms_fp64 = max_over_ranks([statistics.mean(t_mixed), statistics.mean(t_fp64)], world)
 
     # end to end through the public API with host buffers (pinned)
     h_init = torch.from_numpy(np.ascontiguousarray(psi0)).pin_memory()
