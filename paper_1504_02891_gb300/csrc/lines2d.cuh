@@ -288,9 +288,10 @@ __global__ void __launch_bounds__(lines_y_threads<T>()) k_lines_y(PassGeom<T> G,
 // tile, tile + tiles_per_inst, ...; the next group's input and this group's
 // epilogue operands are fetched with cp.async (each thread its own points)
 // while the transforms run.
+// (at most 128 registers: two CTAs per SM)
 template <typename T, bool CPLX, int EPI, int LF>
-__global__ void __launch_bounds__(LINES_THREADS) k_lines_x(PassGeom<T> G, PassData<T> D, int tiles_per_inst,
-                                                           int groups) {
+__global__ void __launch_bounds__(LINES_THREADS, 2) k_lines_x(PassGeom<T> G, PassData<T> D, int tiles_per_inst,
+                                                              int groups) {
   using FFT = LineFFT<T, LF>;
   using C = typename FFT::C;
   using V = typename VT<T, CPLX>::V;
@@ -325,6 +326,13 @@ __global__ void __launch_bounds__(LINES_THREADS) k_lines_x(PassGeom<T> G, PassDa
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
   T amax = T(0);
+  // H psi sums in float32: each group's 8 (16) points are summed in float and
+  // the group sum enters the float-pair accumulator (float32 data carry no
+  // more digits than that)
+  constexpr bool FPART = EPI == EPI_GRAD && std::is_same<T, float>::value;
+  T pacc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) pacc[q] = T(0);
   const long long ibase = (long long)inst * G.M;
   const T* Vp = D.V;
   LineSym<T, F> sym;
@@ -391,7 +399,15 @@ __global__ void __launch_bounds__(LINES_THREADS) k_lines_x(PassGeom<T> G, PassDa
       else kin = (q < 8) ? v[q].x : v[q - 8].y;
       if (accin) kin = kin + ea[q * NT + tid];
       const V lin = kin + ev[q * NT + tid] * x;
-      epilogue_point<T, CPLX, EPI, false>(E, gi, x, lin, acc, amax);
+      if constexpr (FPART) epilogue_point<T, CPLX, EPI, false>(E, gi, x, lin, pacc, amax);
+      else epilogue_point<T, CPLX, EPI, false>(E, gi, x, lin, acc, amax);
+    }
+    if constexpr (FPART) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        acc_add(acc[q], pacc[q]);
+        pacc[q] = T(0);
+      }
     }
     b ^= 1;
   }
@@ -408,6 +424,36 @@ static int num_sms() {
     if (n <= 0) n = 152;
   }
   return n;
+}
+
+template <typename T, bool CPLX, int EPI, int LF0>
+static gpe_status launch_lines_x(const GridDev<T>& d, const PassData<T>& Dx, int nbatch, int groups,
+                                 cudaStream_t st) {
+  using C = typename C2t<T>::type;
+  const PassGeom<T>& gx = d.geom[0];
+  constexpr int NL = LINES_THREADS / ((1 << LF0) / 8);
+  constexpr int NV = CPLX ? 8 : 16;
+  const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
+  const size_t smem = ((size_t)(1 << LF0) + 2 * (size_t)NL * LineFFT<T, LF0>::P) * sizeof(C) +
+                      3 * (size_t)NV * LINES_THREADS * vsz + (size_t)NV * LINES_THREADS * sizeof(T);
+  static int occ = -1;
+  if (occ < 0) {
+    GPE_CUDA(cudaFuncSetAttribute(k_lines_x<T, CPLX, EPI, LF0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_x<T, CPLX, EPI, LF0>, LINES_THREADS,
+                                                           smem));
+    if (occ < 1) occ = 1;
+  }
+  // about four resident waves in all, at most the reduction scratch's capacity
+  const long long want = 4LL * occ * num_sms();
+  int tiles = groups;
+  while (tiles > 1 && (long long)tiles * nbatch > want) tiles = (tiles + 1) / 2;
+  while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
+  if ((long long)tiles * nbatch > d.max_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
+  ProfScope ps(kernel_name("linesx", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
+  k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, LINES_THREADS, smem, st>>>(gx, Dx, tiles, groups);
+  GPE_CUDA(cudaGetLastError());
+  return GPE_OK;
 }
 
 template <typename T, bool CPLX, int EPI, int LF0, int LF1>
@@ -449,26 +495,8 @@ static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, in
     PassData<T> Dx = D;
     Dx.step_on_load = 0;
     Dx.acc_in = acc;
-    constexpr int NV = CPLX ? 8 : 16;
-    const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
-    const size_t smem = ((size_t)(1 << LF0) + 2 * (size_t)NL * LineFFT<T, LF0>::P) * sizeof(C) +
-                        3 * (size_t)NV * LINES_THREADS * vsz + (size_t)NV * LINES_THREADS * sizeof(T);
-    static int occ = -1;
-    if (occ < 0) {
-      GPE_CUDA(cudaFuncSetAttribute(k_lines_x<T, CPLX, EPI, LF0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-      GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_x<T, CPLX, EPI, LF0>, LINES_THREADS, smem));
-      if (occ < 1) occ = 1;
-    }
-    // about four resident waves in all, at most the reduction scratch's capacity
-    const long long want = 4LL * occ * num_sms();
-    int tiles = groups;
-    while (tiles > 1 && (long long)tiles * nbatch > want) tiles = (tiles + 1) / 2;
-    while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
-    if ((long long)tiles * nbatch > d.max_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
-    ProfScope ps(kernel_name("linesx", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
-    k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, LINES_THREADS, smem, st>>>(gx, Dx, tiles, groups);
-    GPE_CUDA(cudaGetLastError());
+    gpe_status s = launch_lines_x<T, CPLX, EPI, LF0>(d, Dx, nbatch, groups, st);
+    if (s != GPE_OK) return s;
   }
   return GPE_OK;
 }

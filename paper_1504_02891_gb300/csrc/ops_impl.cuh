@@ -63,6 +63,7 @@ __device__ __forceinline__ void acc_add(DF& a, float b) {
   a.lo += err;
 }
 __device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(float& a, float b) { a += b; }   // short float partials
 __device__ __forceinline__ void acc_merge(DF& a, const DF& b) {
   acc_add(a, b.hi);
   a.lo += b.lo;
