@@ -235,6 +235,19 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
       float amax = 0.f;
+      // per-thread sums: up to 8 points in float, then into the float pairs
+      float pacc[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) pacc[q] = 0.f;
+      int npart = 0;
+      auto merge = [&]() {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          acc_add(acc[q], pacc[q]);
+          pacc[q] = 0.f;
+        }
+        npart = 0;
+      };
       if constexpr (SHIFT) {
         const float al = (float)s_ctl.alpha, de = (float)s_ctl.delta, thk = (float)s_ctl.theta_ref;
         const float thc = (float)(hc ? s_ctl.theta_c : s_ctl.theta_hint);
@@ -250,25 +263,26 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
           const V gh = pk + hD + (de - thk) * y;
           Gt[i] = gh;
           const V x = xk + y;
-          acc_add(acc[Q_WX], tre(pk, y) + thk * R + 0.5f * tre(y, hD) + 0.5f * de * tre(y, y));
-          acc_add(acc[Q_NY], tre(x, x));
-          acc_add(acc[Q_YG], tre(x, gh));
-          acc_add(acc[Q_GG], tre(gh, gh));
+          acc_add(pacc[Q_WX], tre(pk, y) + thk * R + 0.5f * tre(y, hD) + 0.5f * de * tre(y, y));
+          acc_add(pacc[Q_NY], tre(x, x));
+          acc_add(pacc[Q_YG], tre(x, gh));
+          acc_add(pacc[Q_GG], tre(gh, gh));
           const V q = gh - thc * x;
-          acc_add(acc[Q_Q], tre(q, q));
-          acc_add(acc[Q_QY], tre(q, x));
+          acc_add(pacc[Q_Q], tre(q, q));
+          acc_add(pacc[Q_QY], tre(q, x));
           const V yc = Xc ? Xc[i] : vzero<V>();
           const V gc = Gc ? Gc[i] : vzero<V>();
           const V sv = y - yc;
           const V vv = (gh - gc) - thc * sv;
           const float s2 = tre(sv, sv);
-          acc_add(acc[Q_SS], s2);
-          acc_add(acc[Q_SV], tre(sv, vv));
-          acc_add(acc[Q_VV], tre(vv, vv));
-          acc_add(acc[Q_VY], tre(vv, x));
-          acc_add(acc[Q_SY], tre(sv, x));
-          acc_add(acc[Q_DF], tre(sv, q) - 0.5f * tre(sv, vv));   // W quadratic: trapezoid exact
+          acc_add(pacc[Q_SS], s2);
+          acc_add(pacc[Q_SV], tre(sv, vv));
+          acc_add(pacc[Q_VV], tre(vv, vv));
+          acc_add(pacc[Q_VY], tre(vv, x));
+          acc_add(pacc[Q_SY], tre(sv, x));
+          acc_add(pacc[Q_DF], tre(sv, q) - 0.5f * tre(sv, vv));   // W quadratic: trapezoid exact
           amax = fmaxf(amax, s2);
+          if (++npart == 8) merge();
         }
       } else {
         EpiCtx<float, CPLX> E;
@@ -285,9 +299,11 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         for (int i = tid; i < nloc; i += nt) {
           const V y = Xt[i];
           const V lin = K[i] + Vs[i] * y;
-          epilogue_point<float, CPLX, EPI_F, false>(E, i, y, lin, acc, amax);
+          epilogue_point<float, CPLX, EPI_F, false>(E, i, y, lin, pacc, amax);
+          if (++npart == 8) merge();
         }
       }
+      merge();
       block_partial(acc, amax, NQ, part);
       stamp(inst, loop, 6);
       cl.sync();

@@ -554,16 +554,16 @@ static __device__ bool grid_barrier(unsigned int* bar, int* err) {
 static __device__ void set_coef(Alg1Ctl* c) {
   const double t = c->tau, nX = c->nX, XG = c->XG, GG = c->GG, PP = c->PP;
   const double nxpp = nX * PP;                       // nX*GG - XG^2, cancellation-free
-  const double den = 1.0 + t * t * nxpp;
-  const double a = (1.0 + 2.0 * t * XG - t * t * nxpp) / den;
-  const double b = -2.0 * t * nX / den;
+  const double inv = 1.0 / (1.0 + t * t * nxpp);     // one division for a, b and a - 1
+  const double a = (1.0 + 2.0 * t * XG - t * t * nxpp) * inv;
+  const double b = -2.0 * t * nX * inv;
   const double ny = a * a * nX + 2.0 * a * b * XG + b * b * GG;
   double s = 1.0 / sqrt(ny);
   if (!c->always_renorm && fabs(ny - 1.0) <= c->renorm_tol) s = 1.0;
   c->a = a;
   c->b = b;
   c->s = s;
-  c->am1 = (2.0 * t * XG - 2.0 * t * t * nxpp) / den;   // a - 1
+  c->am1 = (2.0 * t * XG - 2.0 * t * t * nxpp) * inv;   // a - 1
 }
 
 // Algorithm 1 after an evaluation at the trial point: the nonmonotone test of
@@ -642,7 +642,7 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
     c->Q = Qn;
     c->k += 1;
     c->tau_last = c->tau;
-    if (c->eps0 > 0.0 && r[Q_MAX] / c->tau <= c->eps0) { c->done = 1; c->status = 0; }
+    if (c->eps0 > 0.0 && r[Q_MAX] <= c->eps0 * c->tau) { c->done = 1; c->status = 0; }   // Eq. crit1, tau > 0
     double tb;
     if ((c->k & 1) == 0) tb = fabs(SW) > 0.0 ? SS / fabs(SW) : 1e20;
     else tb = WW > 0.0 ? fabs(SW) / WW : 1e20;
