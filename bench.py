@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 256 << 20
 # Cayley step formed in the first pass's load (read X_c, G_c, write G_new, plus
 # the trial point Y); the ratio pass (read Z, X^k, G^k).  Per real number: 4 B
 # (float32) or 8 B (float64); complex doubles it.
-ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3}
+ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5, "acc": 2}
 # DRAM bytes (read + write) of one H psi apply of the happly workload, from the
 # ncu capture summarised in profiles/happly_64x512sq_c64_lines.txt (k_lines_y
 # 227.6 MB + k_lines_x 374.0 MB); must be re-taken whenever those kernels change.
@@ -210,7 +210,7 @@ def roofline_from_profile(prof, peaks):
     napp = sum(g["final"].values())
     kind = max(g["final"], key=lambda k: g["final"][k]) if g["final"] else "grad"
     real_bytes = 4 if prec == "f32" else 8
-    per_point = sum(ALG_REALS_PER_POINT[k] * c for k, c in g["final"].items()) / max(napp, 1)
+    per_point = sum(ALG_REALS_PER_POINT.get(k, 2) * c for k, c in g["final"].items()) / max(napp, 1)
     per_point *= real_bytes * (2 if cplx == "c" else 1)
     t_app = g["ms"] / max(napp, 1) * 1e-3
     achieved = per_point * M / t_app / 1e9

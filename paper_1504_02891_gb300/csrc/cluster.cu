@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
   double* part = reinterpret_cast<double*>(f1 + A.lch * Pm);
   __shared__ Alg1Ctl s_ctl;
   __shared__ double s_res[NQ];
+  __shared__ float2 s_gath[16 * NQ];   // every CTA's partials, pushed by their owners
   using Acc = DF;
 
   for (int i = tid; i < n0; i += nt) tw0[i] = A.tw0[i];
@@ -305,6 +306,16 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       merge();
       block_partial(acc, amax, NQ, part);
+      // push this CTA's partials into every CTA's gather array (remote stores
+      // do not wait; the barrier below makes them visible), so that the fold
+      // reads local shared memory only.  The previous iteration's reads of
+      // s_gath are separated from these writes by the two barriers of this
+      // iteration's line passes.
+      for (int idx = tid; idx < cs * NQ; idx += nt) {
+        const int r = idx / NQ, q = idx - r * NQ;
+        float2* dst = cl.map_shared_rank(s_gath, r);
+        dst[rank * NQ + q] = reinterpret_cast<const float2*>(part)[q];
+      }
       stamp(inst, loop, 6);
       cl.sync();
       // 7. fold the cluster's partials in rank order, then the control on the local copy
@@ -313,8 +324,10 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         DF v;
         acc_zero(v);
         for (int r = 0; r < cs; ++r) {
-          const DF* rp = reinterpret_cast<const DF*>(cl.map_shared_rank(part, r));
-          const DF w = rp[q];
+          const float2 f = s_gath[r * NQ + q];
+          DF w;
+          w.hi = f.x;
+          w.lo = f.y;
           if (q == Q_MAX) v.hi = fmaxf(v.hi, w.hi);
           else acc_merge(v, w);
         }
@@ -345,15 +358,17 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
 // Cluster size, chunk and shared memory for an n0 x n1 grid; false if the
 // state does not fit in a 16-CTA cluster.
 bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs_out, int* lch_out, int* P0, int* P1, size_t* smem_out,
-                   unsigned int* vec_bytes, unsigned int* vpot_bytes) {
+                   unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share) {
   const size_t vsz = cplx ? 8 : 4;
   const size_t total = (size_t)n0 * n1 * vsz;
-  // smallest cluster whose per-CTA share of a vector is <= 16 KiB (more CTAs
-  // share the FFT work), else the largest that fits
+  // smallest cluster whose per-CTA share of a vector is <= share (more CTAs
+  // share the work of one instance: 4 KiB for a single solve, where latency
+  // counts; 16 KiB for a batch, where SMs are better spent on more instances),
+  // else the largest that fits
   int pick = -1;
   for (int cs = 1; cs <= 16; cs *= 2) {
     if (n1 / cs < (cplx ? 1 : 2) || n0 / cs < (cplx ? 1 : 2)) break;
-    if (total / cs <= 16 * 1024) { pick = cs; break; }
+    if (total / cs <= share) { pick = cs; break; }
     if (total / cs <= 48 * 1024) pick = cs;
   }
   if (pick < 0) return false;
@@ -395,7 +410,8 @@ gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st) {
   int cs, lch, P0, P1;
   size_t smem;
   unsigned int vb, vp;
-  if (!cluster_shape(A.n0, A.n1, cplx, A.shifted ? 7 : 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp))
+  if (!cluster_shape(A.n0, A.n1, cplx, A.shifted ? 7 : 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp,
+                     (size_t)(A.share_kb > 0 ? A.share_kb : 16) * 1024))
     return fail(GPE_EINVAL, "grid too large for the cluster engine");
   A.cs = cs;
   A.logcs = ilog2i(cs);

@@ -176,6 +176,7 @@ struct ClusterArgs {
   int shifted;             // 1: regularized Newton subproblem in difference form (see cluster.cu)
   const void* xk;          // shifted: X^k (float32) [ninst][n1][n0]
   const void* pk;          // shifted: P_k = G_k - theta_k X^k (float32)
+  int share_kb;            // cluster size: smallest with a per-CTA vector share <= this (KiB; 0: 16)
   unsigned int* next;      // instance counter (zero at launch): clusters take the next
                            // unstarted instance when they finish one; null: round robin
 };

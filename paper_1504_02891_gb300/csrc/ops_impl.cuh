@@ -551,7 +551,7 @@ static __device__ bool grid_barrier(unsigned int* bar, int* err) {
 // ----------------------------------------------------------------- solver control
 // Cayley coefficients of Theorem 3.3 for the current point and step tau, with
 // the §4 renormalisation folded in as the scale s.
-static __device__ void set_coef(Alg1Ctl* c) {
+static __device__ __forceinline__ void set_coef(Alg1Ctl* c) {
   const double t = c->tau, nX = c->nX, XG = c->XG, GG = c->GG, PP = c->PP;
   const double nxpp = nX * PP;                       // nX*GG - XG^2, cancellation-free
   const double inv = 1.0 / (1.0 + t * t * nxpp);     // one division for a, b and a - 1
@@ -571,7 +571,7 @@ static __device__ void set_coef(Alg1Ctl* c) {
 // and the next Barzilai-Borwein step of Eq. bb-1 (alternating tau^{k,1} on even
 // k and tau^{k,2} on odd k; projected-gradient differences formed with the
 // theta shift so that no large terms cancel).
-static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
+static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const double* r) {
   const double obj = (c->objective == 0) ? r[Q_E2] + c->alpha * r[Q_E4] : r[Q_E2] + r[Q_WX];
   const double nY = r[Q_NY], YG = r[Q_YG];
   c->obj_last = obj;
@@ -664,6 +664,18 @@ static __device__ void alg1_control(Alg1Ctl* c, const double* r) {
   }
   if (!c->done && c->k >= c->max_iter) { c->done = 1; c->status = 5; }
   set_coef(c);
+}
+
+// The control on a register copy of the block and of the sums: the fields are
+// read and written back once instead of one dependent shared- or global-memory
+// access per use (the control is a single thread's serial chain).
+static __device__ void alg1_control(Alg1Ctl* cp, const double* rp) {
+  Alg1Ctl c = *cp;
+  double r[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) r[q] = rp[q];
+  alg1_control_impl(&c, r);
+  *cp = c;
 }
 
 // Eq. TR-ratio with both reductions in difference form, Eq. update-X and

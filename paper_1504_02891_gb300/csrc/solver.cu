@@ -598,6 +598,7 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
+  A.share_kb = 4;          // a single solve: latency counts, spread it over more CTAs
   gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
   if (A.dbg) cluster_debug_report(st, A.dbg_n);
@@ -683,6 +684,7 @@ static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double
   A.shifted = 1;
   A.xk = Lf.xk;
   A.pk = Lf.gk;
+  A.share_kb = 4;          // a single solve: latency counts, spread it over more CTAs
   gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
   s = read_ctl<float>(Lf, st);
