@@ -395,3 +395,73 @@ def test_fd_prolongation_linear_exact():
     pro = O.prolong(gc, gf, tent(gc.nodes[0]))
     ff = tent(gf.nodes[0])
     assert np.max(np.abs(pro * math.sqrt(O.norm2(gf, ff)) - ff)) < 1e-12
+
+
+# ---------------------------------------------------------------- second-order certificate
+
+def _dense_hlin(g):
+    M = g.V.size
+    cplx = g.is_complex
+    H = np.zeros((M, M), complex if cplx else float)
+    for k in range(M):
+        e = np.zeros(M, complex if cplx else float)
+        e[k] = 1.0
+        H[:, k] = O.apply_hlin(g, e.reshape(g.shape)).ravel()
+    return 0.5 * (H + H.conj().T)
+
+
+def test_certificate_beta0_ground_and_first_excited_states():
+    """beta = 0: grad^2 F - theta on T_X equals 2 (H_lin - lambda) restricted to
+    the complement of the state, so the certificate is 2 (lambda_1 - lambda_0)
+    at the ground state and 2 (lambda_0 - lambda_1) at the first excited state
+    (lambda_i from numpy eigh of the explicit matrix); the 1D harmonic trap has
+    lambda_1 - lambda_0 = 1 to grid accuracy (Lemma 3.2: a minimiser and a
+    saddle)."""
+    p = W.problem(1, (64,), (-8.0,), (8.0,), "fourier", beta=0.0)
+    g = O.build_grid(p)
+    lam, vec = np.linalg.eigh(_dense_hlin(g))
+    gap = lam[1] - lam[0]
+    assert abs(gap - 1.0) < 1e-9
+    c0, D0 = O.tangent_hessian_min(g, vec[:, 0].reshape(g.shape))
+    c1, _ = O.tangent_hessian_min(g, vec[:, 1].reshape(g.shape))
+    assert abs(c0 - 2.0 * gap) < 1e-9
+    assert abs(c1 + 2.0 * gap) < 1e-9
+    # the minimiser is the first excited state (up to sign), tangent to X
+    assert abs(abs(np.dot(D0.ravel(), vec[:, 1])) - 1.0) < 1e-8
+
+
+def test_certificate_complex_data_exclude_the_phase_mode():
+    """Complex data, beta = 0, Omega = 0, 2D harmonic: iX is tangent in the
+    real sense and a zero mode, but T_X = {D : X^* D = 0} (Eq. tangent-St)
+    excludes it, so the certificate is the gap 2 (lambda_1 - lambda_0) = 2."""
+    p = W.problem(2, (16, 16), (-6.0, -6.0), (6.0, 6.0), "fourier", beta=0.0, is_complex=True)
+    g = O.build_grid(p)
+    lam, vec = np.linalg.eigh(_dense_hlin(g))
+    c0, _ = O.tangent_hessian_min(g, vec[:, 0].reshape(g.shape))
+    assert abs(c0 - 2.0 * (lam[1] - lam[0])) < 1e-9
+    assert abs(lam[1] - lam[0] - 1.0) < 1e-4     # grid accuracy at h = 0.75
+
+
+def test_certificate_is_a_minimum_over_random_tangent_directions():
+    """beta > 0 ground state (oracle solve): no random tangent direction has a
+    smaller Rayleigh quotient of grad^2 F - theta than the certificate, and the
+    certificate is positive (a strict local minimiser, Lemma 3.2 part 2)."""
+    p = W.problem(1, (48,), (-8.0,), (8.0,), "fourier", beta=40.0)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    X0 = U.to_X(W.gaussian(p))
+    r = O.regularized_newton(U, X0, res_tol=1e-11)
+    X = r.X
+    psi = U.to_psi(X)
+    c, D = O.tangent_hessian_min(g, psi)
+    assert c > 0.0
+    theta = float(np.real(np.vdot(X, U.grad(X))))
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        Z = rng.standard_normal(g.shape)
+        Z = Z - X * float(np.vdot(X, Z))
+        Z /= np.linalg.norm(Z)
+        q = U.hess_quad(X, Z) - theta
+        assert q >= c - 1e-9
+    q = U.hess_quad(X, D) - theta
+    assert abs(q - c) < 1e-9
