@@ -187,6 +187,25 @@ gpe_status gpe_solve_opts_default(gpe_solve_opts* opts);
 gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opts* opts,
                              gpe_solve_report* report);
 
+/* Second-order certificate of a stationary state (Lemma 3.2, Eq. sec-opt):
+ * the smallest value of grad^2 F(X)[D, D] - theta D^*D over unit D in the
+ * tangent set T_X = {D : X^*D = 0} (Eq. tangent-St), in the unified units of
+ * Eq. prob (X = sqrt(h_vol) psi, theta = 2 mu; equal to twice the smallest
+ * eigenvalue of P (H'' - mu) P in grid units, H'' as in gpe_hessvec and P the
+ * projector onto the complement of psi and, for complex data, i psi).  A
+ * negative value shows a saddle (not a minimiser); a local minimiser has a
+ * value >= 0, and for complex data the phase direction i psi is excluded.
+ * psi: device grid function of the plan (nbatch = 1), a stationary state for
+ * the test to be meaningful (any state is accepted).  Lanczos with full
+ * reorthogonalisation from a fixed pseudo-random start vector, at most
+ * max_iter (2..1000) steps, until the Ritz residual estimate is below
+ * tol * max(1, |value|).  lambda_min receives the value; residual (may be
+ * NULL) the true residual norm of the Ritz pair in the same units; iters (may
+ * be NULL) the Lanczos steps taken.  Allocates its Lanczos vectors per call
+ * (max_iter + 3 grid functions) and synchronises the plan's stream. */
+gpe_status gpe_hess_min_eig(gpe_plan plan, const void* psi, int max_iter, double tol, double* lambda_min,
+                            double* residual, int* iters);
+
 /* Many independent ground-state problems in one call: Algorithm 1 (Theorem
  * 3.3 step, Eq. bb-1 BB step, Eq. NMLS-Armijo search) in float32 with float64
  * reductions and device-side control for every instance at once -- the

@@ -116,12 +116,20 @@ def load():
         "gpe_prolong": ([vp, vp, vp, vp], ip),
         "gpe_solve_opts_default": ([C.POINTER(SolveOpts)], ip),
         "gpe_rnewton_solve": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveReport)], ip),
+        "gpe_hess_min_eig": ([vp, vp, ip, C.c_double, dp, dp, C.POINTER(C.c_int)], ip),
         "gpe_solve_batch": ([C.POINTER(Problem), ip, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(SolveReport),
                              vp], ip),
         "gpe_kernel_launches": ([], C.c_int64),
         "gpe_profile_enable": ([ip], ip),
         "gpe_profile_summary": ([C.c_char_p, ip], ip),
     }
+    missing = [name for name in sig if not hasattr(L, name)]
+    if missing:
+        # a stale build: release it so that a rebuilt library can be loaded
+        import _ctypes
+        _ctypes.dlclose(L._handle)
+        raise ImportError(f"{LIB_PATH} lacks {', '.join(missing)}; rebuild with "
+                          "`python -m paper_1504_02891_gb300.build`")
     for name, (args, res) in sig.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -133,8 +141,9 @@ def load():
 lib = None
 try:
     lib = load()
-except ImportError:
-    # The module stays importable for build(); every call below raises.
+except (ImportError, OSError):
+    # Not built yet, or a stale build that lacks a newer entry point: the
+    # module stays importable for build(); every call below raises.
     lib = None
 
 
@@ -240,6 +249,15 @@ class Plan:
         self._chk(out)
         _check(load().gpe_hessvec(self.handle, _ptr(psi), _ptr(d), float(shift), _ptr(out)))
         return out
+
+    def hess_min_eig(self, psi, max_iter=200, tol=1e-10):
+        """gpe_hess_min_eig: the second-order certificate of Lemma 3.2 at psi,
+        as (value, residual, Lanczos steps)."""
+        self._chk(psi)
+        lam, res, it = C.c_double(), C.c_double(), C.c_int()
+        _check(load().gpe_hess_min_eig(self.handle, _ptr(psi), int(max_iter), float(tol), C.byref(lam),
+                                       C.byref(res), C.byref(it)))
+        return lam.value, res.value, it.value
 
     def feasible_step(self, psi, hpsi, tau, out=None, with_energy=False):
         self._chk(psi)
