@@ -24,6 +24,7 @@ import numpy as np
 __all__ = [
     "problem", "axis_nodes", "array_shape", "cell_volume", "normalise",
     "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep", "sweep_initial", "random_field",
+    "thomas_fermi", "excited_initial",
 ]
 
 
@@ -139,6 +140,51 @@ def rotating_initial(p, kind="c", noise=0.0, seed=1504):
     return normalise(p, psi)
 
 
+def _trap(p):
+    """The trap of the problem on the grid (its definition: Eq. harmpen, plus
+    the lattice term of Eq. optic98 / Eq. asypon), as initial-data input."""
+    xs = _mesh(p)
+    pot = p["potential"]
+    g = pot["gamma"]
+    V = np.zeros(array_shape(p))
+    for a, x in enumerate(xs):
+        V = V + 0.5 * g[a] ** 2 * x * x
+        if pot["kind"] == "lattice":
+            V = V + pot["depth"] * np.sin(pot["k"] * x) ** 2
+    if pot["kind"] not in ("harmonic", "lattice"):
+        raise ValueError("Thomas-Fermi data for harmonic or lattice traps only")
+    return V
+
+
+def thomas_fermi(p):
+    """The Thomas-Fermi initial data of Eq. TFA, normalised on the grid:
+    phi_0 = sqrt((mu_TF - V)/beta) where V <= mu_TF, else 0, with mu_TF =
+    (3 beta / 2)^(2/3) / 2, (beta gamma_y / pi)^(1/2) and
+    (15 beta gamma_y gamma_z / (4 pi))^(2/5) / 2 for d = 1, 2, 3 (gamma_x = 1)."""
+    d, beta = p["dim"], p["beta"]
+    gy, gz = p["potential"]["gamma"][1], p["potential"]["gamma"][2]
+    if d == 1:
+        mu = 0.5 * (1.5 * beta) ** (2.0 / 3.0)
+    elif d == 2:
+        mu = math.sqrt(beta * gy / math.pi)
+    else:
+        mu = 0.5 * (15.0 * beta * gy * gz / (4.0 * math.pi)) ** 0.4
+    phi = np.sqrt(np.maximum(mu - _trap(p), 0.0) / beta)
+    if p["is_complex"]:
+        phi = phi.astype(np.complex128)
+    return normalise(p, phi)
+
+
+def excited_initial(p, kind):
+    """Asymmetric initial data of §4.4 (2D): "10" sqrt(2) x e^{-r^2/2}/sqrt(pi),
+    "01" the same in y, "11" 2 x y e^{-r^2/2}/sqrt(pi); normalised on the grid."""
+    x, y = _mesh(p)[:2]
+    e = np.exp(-(x * x + y * y) / 2.0) / math.sqrt(math.pi)
+    f = {"10": math.sqrt(2.0) * x * e, "01": math.sqrt(2.0) * y * e, "11": 2.0 * x * y * e}[kind]
+    f = np.broadcast_to(f, array_shape(p)).astype(np.float64)
+    return normalise(p, f)
+
+
 _LATTICE_K = math.pi / 4.0
 
 
@@ -159,6 +205,15 @@ def config(name):
     if name == "c4":      # 2D rotating, Fourier 512^2, Omega=0.9, beta=1000
         return problem(2, (512, 512), (-16.0, -16.0), (16.0, 16.0), "fourier",
                        beta=1000.0, omega=0.9, is_complex=True)
+    if name == "t10":     # §4.4, Table 10: 2D sine (-16,16)^2, 257 nodes, harmonic + 50 lattice, beta=500
+        return problem(2, (256, 256), (-16.0, -16.0), (16.0, 16.0), "sine", beta=500.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0), "depth": 50.0, "k": _LATTICE_K})
+    if name == "t5_100":  # §4.2, Table 5: 3D sine (-8,8)^3, 129^3 nodes, lattice 50, beta=100
+        return problem(3, (128,) * 3, (-8.0,) * 3, (8.0,) * 3, "sine", beta=100.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0, 1.0), "depth": 50.0, "k": _LATTICE_K})
+    if name == "t5_6400":  # §4.2, Table 5: 3D sine (-12,12)^3, 129^3 nodes, lattice 50, beta=6400
+        return problem(3, (128,) * 3, (-12.0,) * 3, (12.0,) * 3, "sine", beta=6400.0,
+                       potential={"kind": "lattice", "gamma": (1.0, 1.0, 1.0), "depth": 50.0, "k": _LATTICE_K})
     if name == "1d_case2":  # §4.1 Case II (sine): V = x^2/2 + 25 sin^2(pi x/4), beta=250
         return problem(1, (256,), (-16.0,), (16.0,), "sine", beta=250.0,
                        potential={"kind": "lattice", "gamma": (1.0,), "depth": 25.0,
@@ -166,7 +221,7 @@ def config(name):
     raise KeyError(name)
 
 
-CONFIGS = ("c1", "c2", "c3", "c3p", "c4", "1d_case2")
+CONFIGS = ("c1", "c2", "c3", "c3p", "c4", "1d_case2", "t10", "t5_100", "t5_6400")
 
 
 def batched_sweep(count=256, seed=20150410):
