@@ -89,9 +89,13 @@ def cayley_step(X, G, tau):
     """
     xg = float(np.real(np.vdot(X, G)))
     nx = float(np.real(np.vdot(X, X)))
-    ng = float(np.real(np.vdot(G, G)))
-    den = 1.0 - tau * tau * xg * xg + tau * tau * nx * ng
-    a = ((1.0 + tau * xg) ** 2 - tau * tau * nx * ng) / den
+    # (X^*X)(G^*G) - (X^*G)^2 >= 0 (Cauchy-Schwarz), evaluated as
+    # (X^*X) |G - (X^*G / X^*X) X|^2 so that rounding cannot make it negative
+    # and the denominator 1 + tau^2 (...) of Theorem 3.3 stays >= 1 for any tau.
+    P = G - (xg / nx) * X
+    cs = nx * float(np.real(np.vdot(P, P)))
+    den = 1.0 + tau * tau * cs
+    a = (1.0 + 2.0 * tau * xg - tau * tau * cs) / den
     b = -2.0 * tau * nx / den
     return a * X + b * G
 
