@@ -465,3 +465,92 @@ def test_certificate_is_a_minimum_over_random_tangent_directions():
         assert q >= c - 1e-9
     q = U.hess_quad(X, D) - theta
     assert abs(q - c) < 1e-9
+
+
+# ---------------------------------------------------------------- accuracy study
+
+def _accuracy_rows(table):
+    path = os.path.join(os.path.dirname(__file__), "golden", "accuracy_tables.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        t, case, disc, h, em, ee, emu = [x.strip() for x in line.split("|")]
+        if t == table:
+            rows.append((case, disc, float(h), float(em), float(ee), float(emu)))
+    return rows
+
+
+def _agrees(ours, printed):
+    """Above the rounding floor within 10%; at the floor (printed < 1e-9) both small."""
+    if printed < 1e-9:
+        return ours < 1e-8
+    return abs(ours / printed - 1.0) <= 0.10
+
+
+# The paper stops Algorithm 1 at Eq. crit1 (eps0 = 1e-6): its energies carry
+# all printed digits, its chemical potentials and widths a few units of the
+# last one (first order in the state's error; the 3D x-widths printed after
+# Table 4 lie 2e-4 below the converged ones in both cases).
+LOOSE = {"mu": 5e-4, "xrms": 3e-4, "yrms": 3e-4, "zrms": 3e-4}
+
+# §4.2 Table 4, SP at h = 2 (7 interior nodes per axis, the stirrer of width 1
+# unresolved): the printed errors belong to a state whose energy is 0.187 away
+# from E_g, while the discrete SP problem has a local minimiser (second-order
+# certificate positive) with a lower energy than either E_g -/+ 0.187.  The row
+# is checked as that inequality, not as printed.
+LOWER_THAN_PRINTED = {("T4", "sine", 2.0)}
+
+
+def _ground_oracle(case, disc, n):
+    p, psi0 = W.accuracy_case(case, disc, n)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    r = O.regularized_newton(U, U.to_X(psi0), res_tol=1e-11)
+    psi = U.to_psi(r.X)
+    psi = psi * np.sign(psi.flat[np.argmax(np.abs(psi))])
+    return p, psi, O.energy(g, psi), O.chem_potential(g, psi)
+
+
+@pytest.mark.parametrize("table,n_fine", [("T1", 512), ("T2", 512), ("T3", 64), ("T4", 64)])
+def test_accuracy_tables(table, n_fine):
+    """§4.1 Tables 1-2 and §4.2 Tables 3-4: FD (second order) and SP (spectral)
+    errors of the ground state against a fine-mesh SP solution, on the paper's
+    meshes, equal to the printed errors (10%, or both at rounding level).  In
+    3D the fine mesh here is h = 1/4 (64 intervals per axis), so the rows at
+    h = 1/4 are left to the GPU test; the 3D fine-mesh state also gives the
+    energy, chemical potential and rms widths printed after Table 4."""
+    rows = _accuracy_rows(table)
+    case = rows[0][0]
+    dim = 1 if case.startswith("1d") else 3
+    L = 32.0 if dim == 1 else 16.0
+    p, pex, Eex, muex = _ground_oracle(case, "sine", n_fine)
+    checked = 0
+    for _, disc, h, em, ee, emu in rows:
+        n = int(round(L / h))
+        if n >= n_fine:
+            continue
+        pc, psi, E, mu = _ground_oracle(case, disc, n)
+        if (table, disc, h) in LOWER_THAN_PRINTED:
+            assert E < Eex - ee
+            assert O.tangent_hessian_min(O.build_grid(pc), psi)[0] > 0.0
+            continue
+        r = n_fine // n
+        err = float(np.max(np.abs(pex[(slice(r - 1, None, r),) * dim] - psi)))
+        for ours, printed, what in ((err, em, "max"), (abs(E - Eex), ee, "E"), (abs(mu - muex), emu, "mu")):
+            assert _agrees(ours, printed), (disc, h, what, ours, printed)
+        checked += 1
+    assert checked >= 5
+    if dim == 3:
+        h = W.cell_volume(p)
+        q = {"E": Eex, "mu": muex}
+        for a, key in enumerate(("xrms", "yrms", "zrms")):
+            x = W.axis_nodes(p, a)
+            shape = [1, 1, 1]
+            shape[2 - a] = x.size
+            q[key] = float(np.sqrt(h * np.sum(x.reshape(shape) ** 2 * pex ** 2)))
+        for (name, k), (v, tol) in paper_values().items():
+            if name != case:
+                continue
+            assert abs(q[k] - v) <= max(tol, LOOSE.get(k, 0.0)), (case, k, q[k], v)

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "problem", "axis_nodes", "array_shape", "cell_volume", "normalise",
     "gaussian", "rotating_initial", "config", "CONFIGS", "batched_sweep", "sweep_initial", "random_field",
-    "thomas_fermi", "excited_initial",
+    "thomas_fermi", "excited_initial", "accuracy_case",
 ]
 
 
@@ -186,6 +186,31 @@ def excited_initial(p, kind):
 
 
 _LATTICE_K = math.pi / 4.0
+
+
+def accuracy_case(case, disc, n):
+    """Problems of the accuracy study (§4.1 Tables 1-2, §4.2 Tables 3-4) with
+    n intervals per axis and discretisation disc ("fd" or "sine"), and the
+    initial data used: 1d_I harmonic beta=400 on (-16,16) (Thomas-Fermi data);
+    1d_II x^2/2 + 25 sin^2(pi x/4), beta=250 (Gaussian); 3d_I gamma (1,2,4),
+    beta=200 on (-8,8)x(-6,6)x(-4,4) (Thomas-Fermi); 3d_II harmonic (1,1,2) +
+    stirrer 4 exp(-((x-1)^2+y^2)), beta=200 on (-8,8)^3 (Gaussian)."""
+    if case == "1d_I":
+        p = problem(1, (n,), (-16.0,), (16.0,), disc, beta=400.0)
+        return p, thomas_fermi(p)
+    if case == "1d_II":
+        p = problem(1, (n,), (-16.0,), (16.0,), disc, beta=250.0,
+                    potential={"kind": "lattice", "gamma": (1.0,), "depth": 25.0, "k": math.pi / 4.0})
+        return p, gaussian(p)
+    if case == "3d_I":
+        p = problem(3, (n,) * 3, (-8.0, -6.0, -4.0), (8.0, 6.0, 4.0), disc, beta=200.0,
+                    potential={"kind": "harmonic", "gamma": (1.0, 2.0, 4.0)})
+        return p, thomas_fermi(p)
+    if case == "3d_II":
+        p = problem(3, (n,) * 3, (-8.0,) * 3, (8.0,) * 3, disc, beta=200.0,
+                    potential={"kind": "stirrer", "gamma": (1.0, 1.0, 2.0), "w0": 4.0, "delta": 1.0, "r0": 1.0})
+        return p, gaussian(p)
+    raise KeyError(case)
 
 
 def config(name):
