@@ -163,6 +163,16 @@ typedef struct {
   int cluster;        /* float32 Algorithm 1 on 2D Fourier grids: one thread-block
                          cluster holds the whole state in distributed shared
                          memory (grids up to 256^2 complex)                      [1] */
+  int search;         /* line search of every Algorithm 1 run: 0 the nonmonotone
+                         search of Eq. NMLS-Armijo from half a BB step (Eq. bb-1);
+                         1 the monotone Armijo search of the Remark after
+                         Theorem 3.4 (Eq. Armijo1): tau = alpha_hat 2^-m, m the
+                         smallest integer (<= 60) with F(Y(tau)) <=
+                         F(X) - rho1 tau ||A(X)X||^2                          [0] */
+  double alpha_hat;   /* search 1: first trial step, > 0 (unified units)      [1e-3] */
+  double eta;         /* search 0: weight of the reference value C^(k) in
+                         Eq. NMLS-Armijo, 0 <= eta < 1 (0: C^(k) = F(X^(k)),
+                         a monotone test from BB steps)                        [0.85] */
 } gpe_solve_opts;
 
 typedef struct {

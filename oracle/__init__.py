@@ -18,13 +18,13 @@ Parity status per function (what pins it) is listed in each module header.
 from .discretize import (Grid, build_grid, potential, apply_kinetic, apply_hlin,
                          energy, energy_parseval, chem_potential, norm2, rms)
 from .unified import (Unified, cayley_step, cayley_dense, proj_grad)
-from .solvers import (feasible_gradient, regularized_newton, prolong, inject,
+from .solvers import (feasible_gradient, armijo_gradient, regularized_newton, prolong, inject,
                       cascadic, SolveResult)
 from .certificate import tangent_hessian_min
 
 __all__ = [
     "Grid", "build_grid", "potential", "apply_kinetic", "apply_hlin", "energy",
     "energy_parseval", "chem_potential", "norm2", "rms", "Unified", "cayley_step",
-    "cayley_dense", "proj_grad", "feasible_gradient", "regularized_newton",
+    "cayley_dense", "proj_grad", "feasible_gradient", "armijo_gradient", "regularized_newton",
     "prolong", "inject", "cascadic", "SolveResult", "tangent_hessian_min",
 ]

@@ -25,7 +25,12 @@ DESIGN.md):
     evenly; sine -- zero-padding of the DST coefficients; FD -- linear
     interpolation; then renormalisation in ||.||_h.
 
-Pins: Algorithm 1/2 reach the beta = 0 ground-state energy (closed form d/2,
+  * Monotone Armijo search (Remark after Theorem 3.4): delta = 1/2, at most
+    60 halvings, alpha_hat given by the caller.
+
+Pins: the monotone search reaches the beta = 0 dense eigenvalue and every
+step it takes is the Armijo point (the step before it fails Eq. Armijo1);
+Algorithm 1/2 reach the beta = 0 ground-state energy (closed form d/2,
 and the smallest eigenvalue of the dense operator on tiny grids), the printed
 E, mu, x_rms of §4.1, the virial identity for harmonic traps and the
 Thomas-Fermi limit; prolongation is exact on band-limited data and injects.
@@ -104,6 +109,49 @@ def feasible_gradient(fg, X0, *, tau0=1e-3, rho1=1e-4, eta=0.85, delta_bt=0.1,
         Qn = eta * Q + 1.0
         C = (eta * Q * C + F) / Qn
         Q = Qn
+        k += 1
+        step_inf = float(np.max(np.abs(X - Xp)))
+        if record:
+            hist.append((F, math.sqrt(inner(P, P)), tau, step_inf))
+        if step_inf / tau <= eps0:
+            break
+    return SolveResult(X, F, k, nfe, math.sqrt(inner(P, P)), hist)
+
+
+def armijo_gradient(fg, X0, *, alpha_hat=1.0, rho1=1e-4, delta_bt=0.5, max_bt=60,
+                    max_iter=2000, eps0=1e-6, res_tol=0.0, renorm_tol=1e-14, record=False):
+    """Algorithm 1 with the monotone Armijo search of the Remark after
+    Theorem 3.4: tau^(k) = alpha_hat * delta^m with m the smallest nonnegative
+    integer such that F(Y(tau)) <= F(X^k) - rho1 tau ||A(X^k) X^k||_2^2
+    (Eq. Armijo1); then X^(k+1) = Y(tau^(k)).  Same Cayley curve, stopping
+    tests and renormalisation as feasible_gradient.  At most max_bt
+    reductions; the last one is taken even if the test fails (the test can
+    fail only at rounding level).
+    """
+    X = X0.copy()
+    F, G = fg(X)
+    nfe = 1
+    P = proj_grad(X, G)
+    hist = []
+    k = 0
+    while k < max_iter:
+        pn = math.sqrt(inner(P, P))
+        if res_tol > 0.0 and pn <= res_tol:
+            break
+        tau = alpha_hat
+        for m in range(max_bt + 1):
+            Y = cayley_step(X, G, tau)
+            ny = inner(Y, Y)
+            if abs(ny - 1.0) > renorm_tol:
+                Y = Y / math.sqrt(ny)
+            FY, GY = fg(Y)
+            nfe += 1
+            if FY <= F - rho1 * tau * pn * pn or m == max_bt:
+                break
+            tau *= delta_bt
+        Xp = X
+        X, F, G = Y, FY, GY
+        P = proj_grad(X, G)
         k += 1
         step_inf = float(np.max(np.abs(X - Xp)))
         if record:

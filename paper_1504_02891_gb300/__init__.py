@@ -79,7 +79,7 @@ class SolveOpts(C.Structure):
                 ("k_sub", C.c_int), ("max_outer", C.c_int), ("max_iter", C.c_int), ("eps0", C.c_double),
                 ("delta_stop", C.c_double), ("res_tol", C.c_double), ("delta0", C.c_double),
                 ("switch_rel", C.c_double), ("chunk", C.c_int), ("use_graphs", C.c_int), ("persistent", C.c_int),
-                ("cluster", C.c_int)]
+                ("cluster", C.c_int), ("search", C.c_int), ("alpha_hat", C.c_double), ("eta", C.c_double)]
 
 
 class SolveReport(C.Structure):

@@ -75,7 +75,8 @@ struct Alg1Ctl {
   double best_res;     // smallest res seen (stagnation test)
   int k_best, stall_iters;   // stop after stall_iters accepted steps without a new best (0 = off)
   int two_slots;       // 1: slots cur/trial swap on acceptance (no third slot)
-  int pad1;
+  int monotone;        // 1: monotone Armijo search, tau = alpha_hat delta_bt^m, C = F(X_cur)
+  double alpha_hat;    // first trial step of every monotone search
 };
 
 // Outer state of Algorithm 2 (ratio test), written by the ratio pass.

@@ -632,23 +632,32 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
     c->Cg = 0.0;
     c->Q = 1.0;
     c->k = 0;
-    c->tau = c->tau0;
+    c->tau = c->monotone ? c->alpha_hat : c->tau0;
     c->phase = 1;
     c->has_cur = 1;
   } else {
-    // C+ = (eta Q C + F(Y)) / Q+  =>  C+ - F(Y) = eta Q (Cg - dF) / Q+
-    const double Qn = c->eta * c->Q + 1.0;
-    c->Cg = c->eta * c->Q * (c->Cg - dF) / Qn;
-    c->Q = Qn;
+    if (c->monotone) {
+      // Eq. Armijo1: the reference value is F(X^(k+1)) itself
+      c->Cg = 0.0;
+    } else {
+      // C+ = (eta Q C + F(Y)) / Q+  =>  C+ - F(Y) = eta Q (Cg - dF) / Q+
+      const double Qn = c->eta * c->Q + 1.0;
+      c->Cg = c->eta * c->Q * (c->Cg - dF) / Qn;
+      c->Q = Qn;
+    }
     c->k += 1;
     c->tau_last = c->tau;
     if (c->eps0 > 0.0 && r[Q_MAX] <= c->eps0 * c->tau) { c->done = 1; c->status = 0; }   // Eq. crit1, tau > 0
-    double tb;
-    if ((c->k & 1) == 0) tb = fabs(SW) > 0.0 ? SS / fabs(SW) : 1e20;
-    else tb = WW > 0.0 ? fabs(SW) / WW : 1e20;
-    if (!isfinite(tb)) tb = 1e20;
-    tb = fmin(fmax(tb, 1e-20), 1e20);
-    c->tau = 0.5 * tb;
+    if (c->monotone) {
+      c->tau = c->alpha_hat;   // Remark after Theorem 3.4: every search starts at alpha_hat
+    } else {
+      double tb;
+      if ((c->k & 1) == 0) tb = fabs(SW) > 0.0 ? SS / fabs(SW) : 1e20;
+      else tb = WW > 0.0 ? fabs(SW) / WW : 1e20;
+      if (!isfinite(tb)) tb = 1e20;
+      tb = fmin(fmax(tb, 1e-20), 1e20);
+      c->tau = 0.5 * tb;
+    }
   }
   c->m = 0;
   c->accepted_last = 1;

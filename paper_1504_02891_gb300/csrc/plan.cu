@@ -462,5 +462,8 @@ extern "C" gpe_status gpe_solve_opts_default(gpe_solve_opts* o) {
   o->use_graphs = 1;
   o->persistent = 1;
   o->cluster = 1;
+  o->search = 0;
+  o->alpha_hat = 1e-3;
+  o->eta = 0.85;
   return GPE_OK;
 }

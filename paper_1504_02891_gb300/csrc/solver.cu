@@ -198,9 +198,28 @@ struct RunStats {
 };
 
 struct SolveParams {
-  int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs, persistent, cluster;
-  double eps0, delta_stop, res_tol_X, delta0, switch_rel;
+  int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs, persistent, cluster, search;
+  double eps0, delta_stop, res_tol_X, delta0, switch_rel, alpha_hat, eta;
 };
+
+// Options of the line search: search 0 or 1, alpha_hat > 0, 0 <= eta < 1.
+static bool search_opts_ok(const gpe_solve_opts& o) {
+  return (o.search == 0 || o.search == 1) && o.alpha_hat > 0.0 && o.alpha_hat < 1e20 && o.eta >= 0.0 &&
+         o.eta < 1.0;
+}
+
+// Line search of an Algorithm 1 run: Eq. NMLS-Armijo with weight eta and BB
+// first steps (search 0), or the monotone Armijo search of the Remark after
+// Theorem 3.4 (search 1: tau = alpha_hat 2^-m, at most 60 halvings).
+static void set_search(Alg1Ctl& c, const SolveParams& P) {
+  c.eta = P.eta;
+  if (P.search == 1) {
+    c.monotone = 1;
+    c.alpha_hat = P.alpha_hat;
+    c.delta_bt = 0.5;
+    c.max_bt = 60;
+  }
+}
 
 template <typename T>
 static gpe_status read_ctl(Level<T>& L, cudaStream_t st) {
@@ -298,6 +317,7 @@ static gpe_status alg1_run(Level<T>& L, int objective, int first_slot, int max_i
     c.renorm_tol = 1e300;
     c.theta_ref = theta_ref;
   }
+  set_search(c, P);
   GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   // first evaluation (no step)
   gpe_status s = apply_op<T>(L.g, L.d, L.solver_data(objective), objective_epi(objective), L.acc, false, st);
@@ -555,6 +575,7 @@ static void init_cluster_ctl(Alg1Ctl& c, double alpha, const SolveParams& P, boo
   c.theta_hint = theta_start;
   c.stall_iters = stop_f32 ? 40 : 0;
   c.two_slots = 1;
+  set_search(c, P);
 }
 
 // Algorithm 1 on F in float32 by the cluster engine (2D Fourier grids whose
@@ -662,6 +683,7 @@ static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double
   c.theta_hint = 0.0;
   c.two_slots = 1;
   c.stall_iters = 0;       // sub_tol is relative to ||P_k||: above the float32 floor
+  set_search(c, P);
   GPE_CUDA(cudaMemcpyAsync(Lf.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
   ClusterArgs A{};
   A.n0 = g.ext[0];
@@ -917,6 +939,9 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
   P.use_graphs = o.use_graphs;
   P.persistent = o.persistent;
   P.cluster = o.cluster;
+  P.search = o.search;
+  P.alpha_hat = o.alpha_hat;
+  P.eta = o.eta;
   P.eps0 = o.eps0;
   P.delta_stop = o.delta_stop;
   P.res_tol_X = 2.0 * o.res_tol;     // ||A(X)X||_2 = 2 ||H psi - mu psi||_h
@@ -1005,7 +1030,8 @@ extern "C" gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gp
   if (opts) o = *opts;
   else gpe_solve_opts_default(&o);
   if (o.levels < 1 || o.mode < 0 || o.mode > 2 || o.method < 0 || o.method > 1 || o.chunk < 1 || o.k_init < 0 ||
-      o.k_sub < 1 || o.max_outer < 0 || o.max_iter < 0 || !(o.res_tol >= 0) || !(o.delta0 > 0))
+      o.k_sub < 1 || o.max_outer < 0 || o.max_iter < 0 || !(o.res_tol >= 0) || !(o.delta0 > 0) ||
+      !search_opts_ok(o))
     return fail(GPE_EINVAL, "invalid solve options");
   for (int a = 0; a < plan->g.dim; ++a) {
     const int nc = plan->g.N[a] >> (o.levels - 1);
@@ -1149,7 +1175,7 @@ extern "C" gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* 
   gpe_solve_opts o;
   if (opts) o = *opts;
   else gpe_solve_opts_default(&o);
-  if (o.max_iter < 1 || !(o.res_tol >= 0)) return fail(GPE_EINVAL, "invalid solve options");
+  if (o.max_iter < 1 || !(o.res_tol >= 0) || !search_opts_ok(o)) return fail(GPE_EINVAL, "invalid solve options");
   std::vector<GridHost> gh(n);
   for (int i = 0; i < n; ++i) {
     if (!psi[i]) return fail(GPE_EINVAL, "psi[i] is NULL");
@@ -1165,6 +1191,9 @@ extern "C" gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* 
   }
   SolveParams P{};
   P.max_iter = o.max_iter;
+  P.search = o.search;
+  P.alpha_hat = o.alpha_hat;
+  P.eta = o.eta;
   P.eps0 = o.eps0;
   P.res_tol_X = 2.0 * o.res_tol;
   P.switch_rel = o.switch_rel;

@@ -83,3 +83,32 @@ def test_batch_rejects_unsupported_grids_without_device():
         st = L.gpe_solve_batch(probs, 1, ptrs, None, reps, None)
         assert st == 1, (p["dim"], p["disc"], st)
         assert len(L.gpe_last_error()) > 0
+
+
+def test_solve_options_layout_and_search_validation_without_device():
+    """gpe_solve_opts_default fills the documented values (so the binding's
+    structure matches the header's), and gpe_solve_batch rejects invalid
+    line-search options on the host before any CUDA call."""
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1504_02891_gb300 import build as B
+    B.build()
+    import paper_1504_02891_gb300 as G
+    import workloads as W
+    L = G.load()
+    o = G.SolveOpts()
+    assert L.gpe_solve_opts_default(ctypes.byref(o)) == 0
+    assert (o.levels, o.mode, o.k_sub, o.max_iter, o.chunk, o.cluster) == (1, 1, 200, 2000, 16, 1)
+    assert (o.search, o.alpha_hat, o.eta) == (0, 1e-3, 0.85)
+    p = W.problem(2, (64, 64), (-4, -4), (4, 4), "fourier")
+    probs = (G.Problem * 1)(G.Problem.from_params(p))
+    ptrs = (ctypes.c_void_p * 1)(ctypes.c_void_p(16))
+    reps = (G.SolveReport * 1)()
+    for field, value in (("search", 2), ("alpha_hat", 0.0), ("eta", 1.0), ("eta", -0.1)):
+        bad = G.SolveOpts()
+        L.gpe_solve_opts_default(ctypes.byref(bad))
+        setattr(bad, field, value)
+        st = L.gpe_solve_batch(probs, 1, ptrs, ctypes.byref(bad), reps, None)
+        assert st == 1, (field, value, st)
+        assert b"options" in L.gpe_last_error()

@@ -247,6 +247,59 @@ def test_algorithm1_float32_tracks_oracle():
     assert abs(rep["E"] - r.F) <= 1e-4 * abs(r.F), (rep["E"], r.F)
 
 
+@pytest.mark.parametrize("iters", [1, 3, 12, 40])
+def test_monotone_armijo_iterates_match_oracle(iters):
+    """search = 1 (Remark after Theorem 3.4, Eq. Armijo1): every search starts
+    at alpha_hat and halves; the device follows the oracle's iterates."""
+    p = W.problem(1, (128,), (-12.0,), (12.0,), "fourier", beta=100.0)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    psi0 = W.gaussian(p)
+    r = O.armijo_gradient(U.fg, U.to_X(psi0), alpha_hat=0.01, delta_bt=0.5, max_bt=60, max_iter=iters, eps0=0.0)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, method=1, mode=0, levels=1, max_iter=iters, eps0=0.0, res_tol=0.0,
+                         search=1, alpha_hat=0.01)
+        got = host(t)
+    assert rel(got, U.to_psi(r.X)) <= 1e-9
+    assert abs(rep["E"] - r.F) <= 1e-12 * abs(r.F)
+
+
+def test_monotone_test_with_bb_steps_matches_oracle():
+    """eta = 0 in Eq. NMLS-Armijo (C^(k) = F(X^(k))) with BB first steps, 2D."""
+    p = W.config("c2")
+    p["n"] = (64, 64)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    psi0 = W.gaussian(p)
+    r = O.feasible_gradient(U.fg, U.to_X(psi0), eta=0.0, max_iter=20, eps0=0.0)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, method=1, mode=0, levels=1, max_iter=20, eps0=0.0, res_tol=0.0, eta=0.0)
+        got = host(t)
+    assert rel(got, U.to_psi(r.X)) <= 1e-9
+    assert abs(rep["E"] - r.F) <= 1e-12 * abs(r.F)
+
+
+@pytest.mark.parametrize("mode", [0, 2], ids=["fp64", "fp32_cluster"])
+def test_monotone_armijo_converges_to_ground_state(mode):
+    """search = 1 run to convergence reaches the ground state of the default
+    solver (float64 per-launch path; float32 cluster engine on 2D Fourier)."""
+    p = W.problem(2, (32, 32), (-6.0, -6.0), (6.0, 6.0), "fourier", beta=50.0, omega=0.3, is_complex=True)
+    psi0 = W.gaussian(p, dtype=np.complex128)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        ref = plan.solve(t, res_tol=1e-10)
+    prec = G.F64 if mode == 0 else G.F32
+    with G.Plan(p, prec=prec) as plan:
+        t = G.to_device(psi0, prec)
+        rep = plan.solve(t, method=1, mode=mode, levels=1, max_iter=30000, eps0=0.0,
+                         res_tol=1e-7 if mode == 0 else 0.0, search=1, alpha_hat=0.02,
+                         switch_rel=1e-5)
+    tol = 1e-10 if mode == 0 else 2e-6
+    assert abs(rep["E"] - ref["E"]) <= tol * abs(ref["E"]), (rep, ref["E"])
+
+
 @pytest.mark.parametrize("case", ["c2_128_fp64", "c2_128_mixed", "c3_32_fp64"])
 def test_persistent_launch_matches_per_iteration_launches(case):
     """The persistent Algorithm 1 launch (grid barriers, control in every CTA)

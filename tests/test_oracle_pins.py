@@ -554,3 +554,60 @@ def test_accuracy_tables(table, n_fine):
             if name != case:
                 continue
             assert abs(q[k] - v) <= max(tol, LOOSE.get(k, 0.0)), (case, k, q[k], v)
+
+
+# ---------------------------------------------------------------- monotone Armijo search
+
+def _tiny_rotating(beta=0.0):
+    p = W.problem(2, (8, 8), (-4.0, -4.0), (4.0, 4.0), "fourier", beta=beta, omega=0.4,
+                  is_complex=True, potential={"kind": "harmonic", "gamma": (1.0, 1.3)})
+    g = O.build_grid(p)
+    rng = np.random.default_rng(11)
+    X0 = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    return g, X0 / np.linalg.norm(X0)
+
+
+def test_armijo_tiny_grid_reaches_dense_eigenvalue():
+    """Remark after Theorem 3.4 (Eq. Armijo1), beta = 0: the monotone search
+    reaches min F = smallest eigenvalue of H_lin (numpy eigh of the explicit
+    matrix), from random data."""
+    g, X0 = _tiny_rotating()
+    M = X0.size
+    H = np.zeros((M, M), complex)
+    for k in range(M):
+        e = np.zeros(M, complex)
+        e[k] = 1.0
+        H[:, k] = O.apply_hlin(g, e.reshape(g.shape)).ravel()
+    lam_min = np.linalg.eigvalsh(0.5 * (H + H.conj().T))[0]
+    U = O.Unified(g)
+    r = O.armijo_gradient(U.fg, X0, alpha_hat=0.05, max_iter=20000, eps0=0.0, res_tol=1e-6)
+    assert r.res <= 1e-6
+    assert abs(r.F - lam_min) < 1e-9
+
+
+def test_armijo_steps_are_the_armijo_points():
+    """Each accepted step is alpha_hat delta^m with m the smallest integer
+    meeting Eq. Armijo1 (checked by brute force: the step before it fails),
+    so F decreases monotonically; interacting, rotating data."""
+    g, X0 = _tiny_rotating(beta=40.0)
+    U = O.Unified(g)
+    ah, dl, rho1 = 0.03, 0.5, 1e-4
+    X = X0
+    F, G = U.fg(X)
+    ms = []
+    for k in range(25):
+        P = O.proj_grad(X, G)
+        res2 = float(np.real(np.vdot(P, P)))
+        r = O.armijo_gradient(U.fg, X, alpha_hat=ah, delta_bt=dl, rho1=rho1, max_iter=1, eps0=0.0, record=True)
+        tau = r.history[0][2]
+        m = math.log(ah / tau) / math.log(1.0 / dl)
+        assert abs(m - round(m)) < 1e-9
+        ms.append(round(m))
+        assert r.F <= F - rho1 * tau * res2
+        if round(m) > 0:
+            Y = O.cayley_step(X, G, tau / dl)
+            Y = Y / math.sqrt(float(np.real(np.vdot(Y, Y))))
+            assert U.fg(Y)[0] > F - rho1 * (tau / dl) * res2
+        X = r.X
+        F, G = U.fg(X)
+    assert min(ms) == 0 and max(ms) >= 1, ms
