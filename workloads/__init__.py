@@ -111,12 +111,16 @@ def rotating_initial(p, kind="c", noise=0.0, seed=1504):
 
     phi_a = exp(-(x^2+y^2)/2)/sqrt(pi), phi_b = (x+iy) phi_a; (c) is the
     normalised mean of (a) and (b); (d) mixes them with weights (1-Omega) and
-    Omega.  A bar conjugates.  ``noise`` > 0 multiplies by exp(i*noise*xi),
+    Omega.  A bar conjugates.  In 3D phi_a also carries exp(-gamma_z z^2/2).  ``noise`` > 0 multiplies by exp(i*noise*xi),
     xi iid standard normal from numpy default_rng(seed) in C order, then
     renormalises.
     """
-    x, y = _mesh(p)[:2]
+    xs = _mesh(p)
+    x, y = xs[:2]
     pa = np.exp(-(x * x + y * y) / 2.0) / math.sqrt(math.pi) + 0j
+    if p["dim"] == 3:     # 3D: the trap's Gaussian along z
+        gz = p["potential"]["gamma"][2]
+        pa = pa * np.exp(-0.5 * gz * xs[2] * xs[2])
     pa = np.broadcast_to(pa, array_shape(p)).astype(np.complex128)
     pb = (x + 1j * y) * pa
     base = kind.split("_")[0]
@@ -230,6 +234,9 @@ def config(name):
     if name == "c4":      # 2D rotating, Fourier 512^2, Omega=0.9, beta=1000
         return problem(2, (512, 512), (-16.0, -16.0), (16.0, 16.0), "fourier",
                        beta=1000.0, omega=0.9, is_complex=True)
+    if name == "r3":      # 3D rotating, Fourier 64^3 on (-8,8)^3, gamma (1,1,2), beta=200, Omega=0.7
+        return problem(3, (64,) * 3, (-8.0,) * 3, (8.0,) * 3, "fourier", beta=200.0, omega=0.7,
+                       is_complex=True, potential={"kind": "harmonic", "gamma": (1.0, 1.0, 2.0)})
     if name == "t10":     # §4.4, Table 10: 2D sine (-16,16)^2, 257 nodes, harmonic + 50 lattice, beta=500
         return problem(2, (256, 256), (-16.0, -16.0), (16.0, 16.0), "sine", beta=500.0,
                        potential={"kind": "lattice", "gamma": (1.0, 1.0), "depth": 50.0, "k": _LATTICE_K})
@@ -246,7 +253,7 @@ def config(name):
     raise KeyError(name)
 
 
-CONFIGS = ("c1", "c2", "c3", "c3p", "c4", "1d_case2", "t10", "t5_100", "t5_6400")
+CONFIGS = ("c1", "c2", "c3", "c3p", "c4", "r3", "1d_case2", "t10", "t5_100", "t5_6400")
 
 
 def batched_sweep(count=256, seed=20150410):
