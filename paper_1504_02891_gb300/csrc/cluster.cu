@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         s_res[q] = acc_value(v);
       }
       __syncthreads();
-      if (tid == 0) alg1_control(&s_ctl, s_res);
+      if (tid == 0) alg1_control<float>(&s_ctl, s_res);
       __syncthreads();
       stamp(inst, loop, 7);
     }

@@ -173,15 +173,24 @@ template <typename C> __device__ __forceinline__ C mul_mi(C v) {   // -i v
   return r;
 }
 
+// Complex sum and difference of the butterflies: in float32 one packed
+// two-lane instruction each (a - b as fma(b, -1, a), exactly rounded).
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return a + b; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return a - b; }
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
   const C t = a;
-  a = t + b;
-  b = t - b;
+  a = cadd(t, b);
+  b = csub(t, b);
 }
 template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
-  const C s02 = v0 + v2, d02 = v0 - v2, s13 = v1 + v3, d13 = v1 - v3;
-  v0 = s02 + s13;
-  v2 = s02 - s13;
+  const C s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
   v1 = d02 + mul_mi(d13);
   v3 = d02 - mul_mi(d13);
 }
@@ -196,10 +205,10 @@ template <typename C> __device__ __forceinline__ void dft8(C* v) {
   o1 = cmulc(o1, GPE_R2, -GPE_R2);
   o2 = mul_mi(o2);
   o3 = cmulc(o3, -GPE_R2, -GPE_R2);
-  v[0] = e0 + o0; v[4] = e0 - o0;
-  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
   v[2] = e2 + o2; v[6] = e2 - o2;
-  v[3] = e3 + o3; v[7] = e3 - o3;
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 template <typename C> __device__ __forceinline__ void dft16(C* v) {
   C e[8], o[8];
@@ -219,8 +228,8 @@ template <typename C> __device__ __forceinline__ void dft16(C* v) {
   o[7] = cmulc(o[7], -GPE_C8, -GPE_S8);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    v[i] = e[i] + o[i];
-    v[i + 8] = e[i] - o[i];
+    v[i] = cadd(e[i], o[i]);
+    v[i + 8] = csub(e[i], o[i]);
   }
 }
 template <typename C, int R> __device__ __forceinline__ void dft_r(C* v) {
@@ -549,34 +558,64 @@ static __device__ bool grid_barrier(unsigned int* bar, int* err) {
 }
 
 // ----------------------------------------------------------------- solver control
+// The control of Algorithm 1 is one thread's serial chain of scalar
+// operations once per trial; it runs in the arithmetic type R of the run.
+// Float64 runs keep float64 (R = double).  Float32 runs (R = float) take their
+// sums from float32 data, and use the step coefficients, theta and tau as
+// float32 values, so float32 arithmetic loses nothing they can use, and on
+// this hardware a float64 division or square root has a latency of hundreds
+// of nanoseconds against tens for float32.  The block keeps float64 storage.
+
 // Cayley coefficients of Theorem 3.3 for the current point and step tau, with
 // the §4 renormalisation folded in as the scale s.
+template <typename R>
 static __device__ __forceinline__ void set_coef(Alg1Ctl* c) {
-  const double t = c->tau, nX = c->nX, XG = c->XG, GG = c->GG, PP = c->PP;
-  const double nxpp = nX * PP;                       // nX*GG - XG^2, cancellation-free
-  const double inv = 1.0 / (1.0 + t * t * nxpp);     // one division for a, b and a - 1
-  const double a = (1.0 + 2.0 * t * XG - t * t * nxpp) * inv;
-  const double b = -2.0 * t * nX * inv;
-  const double ny = a * a * nX + 2.0 * a * b * XG + b * b * GG;
-  double s = 1.0 / sqrt(ny);
-  if (!c->always_renorm && fabs(ny - 1.0) <= c->renorm_tol) s = 1.0;
+  const R t = (R)c->tau, nX = (R)c->nX, XG = (R)c->XG, GG = (R)c->GG, PP = (R)c->PP;
+  const R nxpp = nX * PP;                            // nX*GG - XG^2, cancellation-free
+  R a, b, am1;
+  if (sizeof(R) == 4 && t > R(1) && !(nxpp > R(0))) {
+    // float32, A(X)X = 0 to float32 accuracy: the curve stays at X
+    a = R(1);
+    b = R(0);
+    am1 = R(0);
+  } else if (sizeof(R) == 4 && t > R(1)) {
+    // float32: numerator and denominator divided by tau^2 (u = 1/tau), so
+    // that steps up to the 1e20 clamp do not overflow
+    const R u = R(1) / t;
+    const R inv = R(1) / (u * u + nxpp);
+    a = (u * u + R(2) * u * XG - nxpp) * inv;
+    b = R(-2) * u * nX * inv;
+    am1 = (R(2) * u * XG - R(2) * nxpp) * inv;
+  } else {
+    const R inv = R(1) / (R(1) + t * t * nxpp);      // one division for a, b and a - 1
+    a = (R(1) + R(2) * t * XG - t * t * nxpp) * inv;
+    b = R(-2) * t * nX * inv;
+    am1 = (R(2) * t * XG - R(2) * t * t * nxpp) * inv;
+  }
+  // |Y|^2: float64 evaluates a^2 nX + 2ab XG + b^2 GG; in float32 those terms
+  // cancel to rounding noise for large tau, so the identity |Y|^2 = |X|^2 of
+  // Theorem 3.3 (the Cayley curve keeps the norm) is used instead
+  const R ny = sizeof(R) == 4 ? nX : a * a * nX + R(2) * a * b * XG + b * b * GG;
+  R s = R(1) / sqrt(ny);
+  if (!c->always_renorm && fabs(ny - R(1)) <= (R)c->renorm_tol) s = R(1);
   c->a = a;
   c->b = b;
   c->s = s;
-  c->am1 = (2.0 * t * XG - 2.0 * t * t * nxpp) * inv;   // a - 1
+  c->am1 = am1;   // a - 1
 }
 
 // Algorithm 1 after an evaluation at the trial point: the nonmonotone test of
 // Eq. NMLS-Armijo, backtracking, the reference value update (C, Q), Eq. crit1,
 // and the next Barzilai-Borwein step of Eq. bb-1 (alternating tau^{k,1} on even
-// k and tau^{k,2} on odd k; projected-gradient differences formed with the
-// theta shift so that no large terms cancel).
+// k and tau^{k,2} on odd k, clamped), then the coefficients of the next trial.
+// The objective value itself is kept in float64 (reported, never tested).
+template <typename R>
 static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const double* r) {
   const double obj = (c->objective == 0) ? r[Q_E2] + c->alpha * r[Q_E4] : r[Q_E2] + r[Q_WX];
-  const double nY = r[Q_NY], YG = r[Q_YG];
+  const R nY = (R)r[Q_NY], YG = (R)r[Q_YG];
   c->obj_last = obj;
   c->nfe += 1;
-  if (!isfinite(obj) || !isfinite(r[Q_GG]) || !(nY > 0.0)) {
+  if (!isfinite(obj) || !isfinite(r[Q_GG]) || !(nY > R(0))) {
     c->done = 1;
     c->status = 4;  // GPE_ENONFINITE
     return;
@@ -584,26 +623,27 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
   // Eq. NMLS-Armijo relative to the current point: with Cg = C - F(X_cur),
   // F(Y) <= C - rho1 tau res^2 reads dF <= Cg - rho1 tau res^2, dF formed
   // pointwise (no cancellation of two nearly equal objective values)
-  const double dF = r[Q_DF];
+  const R dF = (R)r[Q_DF];
+  const R tau = (R)c->tau, res = (R)c->res;
   bool accept = true;
   if (c->phase != 0) {
-    const double thr = c->Cg - c->rho1 * c->tau * c->res * c->res;
+    const R thr = (R)c->Cg - (R)c->rho1 * tau * res * res;
     accept = (dF <= thr) || (c->m >= c->max_bt);
   }
   if (!accept) {
-    c->tau *= c->delta_bt;
+    c->tau = tau * (R)c->delta_bt;
     c->m += 1;
     c->accepted_last = 0;
-    set_coef(c);
+    set_coef<R>(c);
     return;
   }
-  const double thY = YG / nY;
-  const double dth = thY - (c->has_cur ? c->theta_c : c->theta_hint);
-  double PPn = r[Q_Q] - 2.0 * dth * r[Q_QY] + dth * dth * nY;
-  if (PPn < 0.0) PPn = 0.0;
-  const double SS = r[Q_SS];
-  const double SW = r[Q_SV] - dth * r[Q_SY];
-  const double WW = r[Q_VV] - 2.0 * dth * r[Q_VY] + dth * dth * nY;
+  const R thY = YG / nY;
+  const R dth = thY - (R)(c->has_cur ? c->theta_c : c->theta_hint);
+  R PPn = (R)r[Q_Q] - R(2) * dth * (R)r[Q_QY] + dth * dth * nY;
+  if (PPn < R(0)) PPn = R(0);
+  const R SS = (R)r[Q_SS];
+  const R SW = (R)r[Q_SV] - dth * (R)r[Q_SY];
+  const R WW = (R)r[Q_VV] - R(2) * dth * (R)r[Q_VY] + dth * dth * nY;
   if (c->two_slots) {
     const int oc = c->has_cur ? c->cur : 1 - c->trial;
     c->cur = c->trial;
@@ -620,13 +660,14 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
     c->prev = (tr + 1) % 3;
     c->trial = (tr + 2) % 3;
   }
+  const R resn = nY * sqrt(PPn);
   c->F_cur = obj;
   c->theta_c = thY;
   c->nX = nY;
   c->XG = YG;
   c->GG = r[Q_GG];
   c->PP = PPn;
-  c->res = nY * sqrt(PPn);
+  c->res = resn;
   c->smax = r[Q_MAX];
   if (c->phase == 0) {
     c->Cg = 0.0;
@@ -641,49 +682,51 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
       c->Cg = 0.0;
     } else {
       // C+ = (eta Q C + F(Y)) / Q+  =>  C+ - F(Y) = eta Q (Cg - dF) / Q+
-      const double Qn = c->eta * c->Q + 1.0;
-      c->Cg = c->eta * c->Q * (c->Cg - dF) / Qn;
+      const R eta = (R)c->eta, Q = (R)c->Q;
+      const R Qn = eta * Q + R(1);
+      c->Cg = eta * Q * ((R)c->Cg - dF) / Qn;
       c->Q = Qn;
     }
     c->k += 1;
     c->tau_last = c->tau;
-    if (c->eps0 > 0.0 && r[Q_MAX] <= c->eps0 * c->tau) { c->done = 1; c->status = 0; }   // Eq. crit1, tau > 0
+    if (c->eps0 > 0.0 && (R)r[Q_MAX] <= (R)c->eps0 * tau) { c->done = 1; c->status = 0; }   // Eq. crit1, tau > 0
     if (c->monotone) {
       c->tau = c->alpha_hat;   // Remark after Theorem 3.4: every search starts at alpha_hat
     } else {
-      double tb;
-      if ((c->k & 1) == 0) tb = fabs(SW) > 0.0 ? SS / fabs(SW) : 1e20;
-      else tb = WW > 0.0 ? fabs(SW) / WW : 1e20;
-      if (!isfinite(tb)) tb = 1e20;
-      tb = fmin(fmax(tb, 1e-20), 1e20);
-      c->tau = 0.5 * tb;
+      R tb;
+      if ((c->k & 1) == 0) tb = fabs(SW) > R(0) ? SS / fabs(SW) : R(1e20);
+      else tb = WW > R(0) ? fabs(SW) / WW : R(1e20);
+      if (!isfinite(tb)) tb = R(1e20);
+      tb = fmin(fmax(tb, R(1e-20)), R(1e20));
+      c->tau = R(0.5) * tb;
     }
   }
   c->m = 0;
   c->accepted_last = 1;
-  if (c->res_tol > 0.0 && c->res <= c->res_tol) { c->done = 1; c->status = 0; }
-  if (c->res_rel > 0.0 && c->res <= c->res_rel * fabs(thY)) { c->done = 1; c->status = 0; }
+  if (c->res_tol > 0.0 && resn <= (R)c->res_tol) { c->done = 1; c->status = 0; }
+  if (c->res_rel > 0.0 && resn <= (R)c->res_rel * fabs(thY)) { c->done = 1; c->status = 0; }
   // precision floor: no new smallest residual (by 10%) for stall_iters steps
-  if (c->phase == 1 && (c->k == 0 || c->res < 0.9 * c->best_res)) {
-    c->best_res = c->res;
+  if (c->phase == 1 && (c->k == 0 || resn < R(0.9) * (R)c->best_res)) {
+    c->best_res = resn;
     c->k_best = c->k;
   } else if (c->stall_iters > 0 && c->k - c->k_best >= c->stall_iters) {
     c->done = 1;
     c->status = 0;
   }
   if (!c->done && c->k >= c->max_iter) { c->done = 1; c->status = 5; }
-  set_coef(c);
+  set_coef<R>(c);
 }
 
 // The control on a register copy of the block and of the sums: the fields are
 // read and written back once instead of one dependent shared- or global-memory
 // access per use (the control is a single thread's serial chain).
+template <typename R>
 static __device__ void alg1_control(Alg1Ctl* cp, const double* rp) {
   Alg1Ctl c = *cp;
   double r[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) r[q] = rp[q];
-  alg1_control_impl(&c, r);
+  alg1_control_impl<R>(&c, r);
   *cp = c;
 }
 
@@ -875,7 +918,7 @@ __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& 
 template <typename T>
 __device__ __forceinline__ void run_control(const PassData<T>& D) {
   if (threadIdx.x == 0) {
-    if (D.control == 1) alg1_control(D.ctl, D.results);
+    if (D.control == 1) alg1_control<T>(D.ctl, D.results);
     else if (D.control == 2) rn_control(D.rn, D.results);
   }
 }
@@ -1157,7 +1200,7 @@ __global__ void __launch_bounds__(NTHREADS) k_alg1_persist(PersistArgs<T> P) {
       stamp(loop, 1 + (a < 1 ? a : 1));
     }
     fold_partials<A>(P.D.partials, P.blocks[P.dim - 1], NQ, s_res);
-    if (threadIdx.x == 0) alg1_control(&s_ctl, s_res);
+    if (threadIdx.x == 0) alg1_control<T>(&s_ctl, s_res);
     __syncthreads();
     stamp(loop, 3);
   }
