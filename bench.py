@@ -228,6 +228,7 @@ def happly_throughput(G, torch, W, peaks, reps=20):
     p = W.config("c4")
     nb = 64
     plan = G.Plan(p, nbatch=nb, prec=G.F32)
+    plan.autotune()                # measured launch shapes (untimed)
     psi = plan.empty()
     psi.real.normal_()
     psi.imag.normal_()
@@ -313,6 +314,7 @@ def our_arm(args):
     p = W.config("c2")
     psi0 = W.gaussian(p)
     plan = G.Plan(p, prec=G.F64)
+    plan.autotune(levels=3)        # measured launch shapes for the three cascade grids (untimed)
     init = G.to_device(psi0)
     work = torch.empty_like(init)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -412,6 +414,7 @@ def our_arm(args):
         "E": rep["E"], "mu": rep["mu"], "res": rep["res"], "delta_E_rel_vs_oracle": dE,
         "solver": {k: rep[k] for k in ("outer_f32", "outer_f64", "inner_f32", "inner_f64", "nfe", "ms_f32", "ms_f64")},
         "roofline": happly, "solve_operator_roofline": roof,
+        "autotune": G.autotune_report(),
         "sweep": sweep,
         "cpu_baseline": cpu,
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": nbytes,
@@ -435,6 +438,7 @@ def profiling_run(args):
     if args.only == "happly":
         p = W.config("c4")
         plan = G.Plan(p, nbatch=64, prec=G.F32)
+        plan.autotune()
         psi = plan.empty()
         psi.real.normal_()
         psi.imag.normal_()
@@ -453,6 +457,7 @@ def profiling_run(args):
     else:
         p = W.config("c2")
         plan = G.Plan(p)
+        plan.autotune(levels=3)
         init = G.to_device(W.gaussian(p))
         for _ in range(2):
             t = init.clone()

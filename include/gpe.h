@@ -240,6 +240,27 @@ gpe_status gpe_hess_min_eig(gpe_plan plan, const void* psi, int max_iter, double
 gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* const* psi, const gpe_solve_opts* opts,
                            gpe_solve_report* reports, void* cuda_stream);
 
+/* Measured launch shapes (the paper has no counterpart: an implementation
+ * choice).  For a plan on a 2D Fourier grid, times on the plan's stream:
+ *   - the register-FFT line kernels of the H-apply (gpe_grad) of this grid and
+ *     batch, for 1, 2, 4 and 8 resident waves of CTAs per kernel;
+ *   - the cluster engine of single float32 solves (Algorithm 1, 24 iterations
+ *     from a Gaussian) on this grid and on the `levels` - 1 coarser cascade
+ *     grids, for each per-CTA share of a state vector in {2,...,32} KiB that
+ *     gives a distinct cluster size;
+ * and records the fastest choices in a process-wide table keyed by grid (and
+ * batch), which every later launch on those shapes uses (without an entry:
+ * 4 waves, 4 KiB).  Computed values do not change (reductions may differ by
+ * rounding order).  Other grids: nothing to tune, GPE_OK.  Allocates scratch
+ * of two plan vectors and one solver level per grid; synchronises.  Not
+ * thread-safe with concurrent launches on the tuned shapes.
+ * Errors: GPE_EINVAL (NULL plan, levels outside [1, 8]), GPE_ENOMEM, GPE_ECUDA. */
+gpe_status gpe_plan_autotune(gpe_plan plan, int levels);
+
+/* Text of the choices made by gpe_plan_autotune so far in this process
+ * (NUL-terminated, truncated to buflen).  GPE_EINVAL if buf is NULL or buflen 0. */
+gpe_status gpe_autotune_report(char* buf, size_t buflen);
+
 /* Allocation-free Cayley step (the paper has no counterpart: this is a
  * packaging variant of gpe_feasible_step for callers that cannot call
  * cudaMalloc -- e.g. code running inside a stream capture that must stay free

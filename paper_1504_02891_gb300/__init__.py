@@ -115,6 +115,8 @@ def load():
         "gpe_feasible_step": ([vp, vp, vp, C.c_double, vp, dp], ip),
         "gpe_prolong": ([vp, vp, vp, vp], ip),
         "gpe_solve_opts_default": ([C.POINTER(SolveOpts)], ip),
+        "gpe_plan_autotune": ([vp, ip], ip),
+        "gpe_autotune_report": ([C.c_char_p, C.c_size_t], ip),
         "gpe_rnewton_solve": ([vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveReport)], ip),
         "gpe_hess_min_eig": ([vp, vp, ip, C.c_double, dp, dp, C.POINTER(C.c_int)], ip),
         "gpe_solve_batch": ([C.POINTER(Problem), ip, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(SolveReport),
@@ -278,6 +280,11 @@ class Plan:
         _check(load().gpe_prolong(self.handle, fine.handle, _ptr(psi_c), _ptr(out)))
         return out
 
+    def autotune(self, levels=1):
+        """gpe_plan_autotune: measure and record the launch shapes for this
+        plan's grid (and `levels` - 1 coarser cascade grids)."""
+        _check(load().gpe_plan_autotune(self.handle, levels))
+
     def solve(self, psi, **opts):
         """gpe_rnewton_solve in place on psi; returns the report as a dict."""
         self._chk(psi)
@@ -290,6 +297,13 @@ class Plan:
         r = SolveReport()
         _check(load().gpe_rnewton_solve(self.handle, _ptr(psi), C.byref(o), C.byref(r)), allow=(5,))
         return r.as_dict()
+
+
+def autotune_report():
+    """The choices recorded by gpe_plan_autotune in this process (text)."""
+    buf = C.create_string_buffer(4096)
+    _check(load().gpe_autotune_report(buf, len(buf)))
+    return buf.value.decode()
 
 
 def solve_batch(params_list, psis, stream=None, **opts):

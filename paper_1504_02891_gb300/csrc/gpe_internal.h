@@ -40,6 +40,18 @@ struct GridHost {
 gpe_status grid_from_problem(const gpe_problem* p, int nbatch, GridHost& g);
 GridHost grid_coarsen(const GridHost& g, int levels_down);
 
+// Measured launch shapes (autotune.cu): resident waves of the line kernels
+// (axis 0: x-kernel, 1: y-kernel; 4 without an entry) and the cluster
+// engine's per-CTA share for single solves (4 KiB without an entry).
+int tuned_waves(int axis, int prec64, int cplx, int n0, int n1, int nbatch);
+void set_tuned_waves(int prec64, int cplx, int n0, int n1, int nbatch, int wx, int wy);
+int tuned_share_kb(int n0, int n1, int cplx);
+void set_tuned_share_kb(int n0, int n1, int cplx, int kb);
+// Time the cluster engine's float32 Algorithm 1 on grid g for each distinct
+// cluster size and record the fastest share (solver.cu); *kb = 0 if the grid
+// does not run in the cluster engine.
+gpe_status tune_cluster_share(const GridHost& g, cudaStream_t st, int* kb, double* us_per_trial);
+
 // Device tables and launch geometry of one grid in precision T.
 template <typename T>
 struct GridDev {

@@ -444,8 +444,9 @@ static gpe_status launch_lines_x(const GridDev<T>& d, const PassData<T>& Dx, int
                                                            smem));
     if (occ < 1) occ = 1;
   }
-  // about four resident waves in all, at most the reduction scratch's capacity
-  const long long want = 4LL * occ * num_sms();
+  // a few resident waves in all (4, or the measured choice), at most the
+  // reduction scratch's capacity
+  const long long want = (long long)tuned_waves(0, sizeof(T) == 8, CPLX, gx.n0, gx.n1, nbatch) * occ * num_sms();
   int tiles = groups;
   while (tiles > 1 && (long long)tiles * nbatch > want) tiles = (tiles + 1) / 2;
   while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
@@ -485,7 +486,7 @@ static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, in
       if (occ < 1) occ = 1;
     }
     const int total = nbatch * colgroups;
-    const int grid = std::min(total, 4 * occ * num_sms());
+    const int grid = std::min(total, tuned_waves(1, sizeof(T) == 8, CPLX, gx.n0, gx.n1, nbatch) * occ * num_sms());
     ProfScope ps(kernel_name("linesy", sizeof(T) == 8, CPLX, EPI_ACC, gx.M * nbatch), st);
     k_lines_y<T, CPLX, LF1><<<grid, YT, smem, st>>>(gy, Dy, colgroups, total);
     GPE_CUDA(cudaGetLastError());

@@ -619,7 +619,7 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  A.share_kb = 4;          // a single solve: latency counts, spread it over more CTAs
+  A.share_kb = tuned_share_kb(g.ext[0], g.ext[1], g.is_complex);   // single solve: 4 KiB or the measured choice
   gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
   if (A.dbg) cluster_debug_report(st, A.dbg_n);
@@ -706,7 +706,7 @@ static gpe_status sub_run_cluster(Level<float>& Lf, const SolveParams& P, double
   A.shifted = 1;
   A.xk = Lf.xk;
   A.pk = Lf.gk;
-  A.share_kb = 4;          // a single solve: latency counts, spread it over more CTAs
+  A.share_kb = tuned_share_kb(g.ext[0], g.ext[1], g.is_complex);   // single solve: 4 KiB or the measured choice
   gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
   s = read_ctl<float>(Lf, st);
@@ -1015,6 +1015,96 @@ static gpe_status solve_impl(gpe_plan plan, void* psi, const gpe_solve_opts& o, 
   rep.nfe = nfe;
   rep.status = fs.converged ? GPE_OK : GPE_ENOCONV;
   if (o.mode == 2) rep.status = GPE_OK;
+  return GPE_OK;
+}
+
+// Autotuning of the cluster engine's per-CTA share for single solves on grid
+// gh: a float32 Algorithm 1 run of 24 iterations from the trap's Gaussian (unit
+// norm) for every share of {2, 4, 8, 16, 32} KiB that gives a distinct
+// cluster size; the fastest time per trial wins and is recorded.
+gpe_status tune_cluster_share(const GridHost& gh, cudaStream_t st, int* best_kb, double* best_us) {
+  *best_kb = 0;
+  *best_us = 0.0;
+  if (gh.disc != GPE_FOURIER || gh.dim != 2 || gh.v_kind == GPE_V_ARRAY) return GPE_OK;
+  GridHost g = gh;
+  g.nbatch = 1;
+  const int n0 = g.ext[0], n1 = g.ext[1], cplx = g.is_complex;
+  int cs, lch, P0, P1;
+  size_t smem;
+  unsigned int vb, vp;
+  if (!cluster_shape(n0, n1, cplx, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
+  // start point: exp(-(x^2 + y^2)/2), unit 2-norm, float32 (complex: zero imaginary part)
+  const int per = cplx ? 2 : 1;
+  std::vector<float> h((size_t)g.M * per, 0.f);
+  double nrm = 0.0;
+  for (int j = 0; j < n1; ++j)
+    for (int i = 0; i < n0; ++i) {
+      const double x = g.nodes[0][i], y = g.nodes[1][j];
+      const double v = exp(-0.5 * (x * x + y * y));
+      h[((size_t)j * n0 + i) * per] = (float)v;
+      nrm += v * v;
+    }
+  const float sc = (float)(1.0 / sqrt(nrm));
+  for (size_t k = 0; k < h.size(); ++k) h[k] *= sc;
+  Level<float> L;
+  gpe_status s = L.create(g);
+  SolveParams P{};
+  P.max_iter = 24;
+  P.cluster = 1;
+  P.search = 0;
+  P.eta = 0.85;
+  P.alpha_hat = 1e-3;
+  const int saved = tuned_share_kb(n0, n1, cplx);
+  int last_cs = -1, pick = saved;
+  double best = 1e300;
+  const int cand[5] = {2, 4, 8, 16, 32};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s == GPE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    s = fail(GPE_ECUDA, "cudaEventCreate");
+  for (int ci = 0; ci < 5 && s == GPE_OK; ++ci) {
+    if (!cluster_shape(n0, n1, cplx, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp, (size_t)cand[ci] * 1024)) continue;
+    if (cs == last_cs) continue;
+    last_cs = cs;
+    set_tuned_share_kb(n0, n1, cplx, cand[ci]);
+    double ms_sum = 0.0;
+    int nfe_sum = 0;
+    for (int rep = 0; rep < 3 && s == GPE_OK; ++rep) {
+      if (cudaStreamSynchronize(st) != cudaSuccess ||
+          cudaMemcpy(L.xs[0], h.data(), L.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        s = fail(GPE_ECUDA, "autotune start point");
+        break;
+      }
+      LevelStats ls;
+      bool used = false;
+      cudaEventRecord(e0, st);
+      s = fg_run_cluster(L, P, false, st, ls, 0.0, &used);
+      cudaEventRecord(e1, st);
+      if (s != GPE_OK || !used) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) {
+        ms_sum += ms;
+        nfe_sum += ls.nfe;
+      }
+    }
+    if (s == GPE_OK && nfe_sum > 0) {
+      const double us = 1e3 * ms_sum / nfe_sum;
+      if (us < best) {
+        best = us;
+        pick = cand[ci];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  L.destroy();
+  set_tuned_share_kb(n0, n1, cplx, s == GPE_OK ? pick : saved);
+  if (s != GPE_OK) return s;
+  if (best < 1e300) {
+    *best_kb = pick;
+    *best_us = best;
+  }
   return GPE_OK;
 }
 

@@ -112,3 +112,17 @@ def test_solve_options_layout_and_search_validation_without_device():
         st = L.gpe_solve_batch(probs, 1, ptrs, ctypes.byref(bad), reps, None)
         assert st == 1, (field, value, st)
         assert b"options" in L.gpe_last_error()
+
+
+def test_autotune_rejects_bad_arguments_without_device():
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1504_02891_gb300 import build as B
+    B.build()
+    import paper_1504_02891_gb300 as G
+    L = G.load()
+    assert L.gpe_plan_autotune(None, 1) == 1
+    assert L.gpe_autotune_report(None, 16) == 1
+    buf = ctypes.create_string_buffer(64)
+    assert L.gpe_autotune_report(buf, len(buf)) == 0
