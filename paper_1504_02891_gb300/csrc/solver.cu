@@ -590,6 +590,8 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
   size_t smem;
   unsigned int vb, vp;
   if (!cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp)) return GPE_OK;
+  const int share_kb = tuned_share_kb(g.ext[0], g.ext[1], g.is_complex);   // single solve: 4 KiB or the measured choice
+  cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp, (size_t)share_kb * 1024);
   Alg1Ctl& c = *L.h_ctl;
   init_cluster_ctl(c, g.beta / (2.0 * g.hvol), P, stop_f32, theta_start);
   GPE_CUDA(cudaMemcpyAsync(L.ctl, &c, sizeof(Alg1Ctl), cudaMemcpyHostToDevice, st));
@@ -619,7 +621,7 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  A.share_kb = tuned_share_kb(g.ext[0], g.ext[1], g.is_complex);   // single solve: 4 KiB or the measured choice
+  A.share_kb = share_kb;
   gpe_status s = launch_cluster_alg1(A, g.is_complex, st);
   if (s != GPE_OK) return s;
   if (A.dbg) cluster_debug_report(st, A.dbg_n);
