@@ -32,8 +32,9 @@ if ROOT not in sys.path:
 METRIC = ("time-to-ground-state at ΔE≤1e-9, mixed vs FP64 on GB300; "
           "Hψ apply GB/s vs peak")
 WORKLOAD = ("2D non-rotating GPE, Fourier 256^2 on [-16,16]^2, V=(x^2+y^2)/2, beta=1000, real psi, "
-            "Gaussian init, cascade 64^2->128^2->256^2, float32 bulk + float64 refinement "
-            "to ||H psi - mu psi||_h <= 1e-9")
+            "Gaussian init, cascade 64^2->128^2->256^2, float32 bulk + float64 regularized Newton "
+            "until ||H psi - mu psi||_h <= 1e-9 or Eq. crit2 (accepted step <= 1e-8), whichever first; "
+            "|dE|/E vs the float64 oracle reported")
 RES_TOL = 1e-9
 L2_FLUSH_BYTES = 256 << 20
 
