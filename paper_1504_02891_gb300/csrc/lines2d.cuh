@@ -99,7 +99,7 @@ struct LineFFT {
 #pragma unroll
         for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw8(st, r));
       }
-      dft8(v);
+      dft8<C, false>(v);
       if (st + 1 < N8 || TAIL) {
         const int Ns = 1 << (3 * st);
         const int k = j & (Ns - 1);
@@ -120,14 +120,14 @@ struct LineFFT {
       v[3] = cmul(v[3], twt(3));
       v[5] = cmul(v[5], twt(4));
       v[7] = cmul(v[7], twt(5));
-      dft4(v[0], v[2], v[4], v[6]);
-      dft4(v[1], v[3], v[5], v[7]);
+      dft4<C, false>(v[0], v[2], v[4], v[6]);
+      dft4<C, false>(v[1], v[3], v[5], v[7]);
     } else if constexpr (TAIL == 1) {
       // butterflies j + u F/8 (slots u, u + 4)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         v[u + 4] = cmul(v[u + 4], twt(u));
-        dft2(v[u], v[u + 4]);
+        dft2<C, false>(v[u], v[u + 4]);
       }
     }
   }

@@ -173,24 +173,28 @@ template <typename C> __device__ __forceinline__ C mul_mi(C v) {   // -i v
   return r;
 }
 
-// Complex sum and difference of the butterflies: in float32 one packed
-// two-lane instruction each (a - b as fma(b, -1, a), exactly rounded).
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return a + b; }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return a - b; }
-template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
-template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+// Complex sum and difference of the butterflies.  PK: in float32 one packed
+// two-lane instruction each (a - b as fma(b, -1, a), exactly rounded); it
+// trades issue slots for FMA-pipe throughput, which pays in the latency-bound
+// cluster engine and not in the register-FFT line kernels (measured).
+template <bool PK, typename C> __device__ __forceinline__ C cadd(C a, C b) {
+  if constexpr (PK && std::is_same<C, float2>::value) return __fadd2_rn(a, b);
+  else return a + b;
+}
+template <bool PK, typename C> __device__ __forceinline__ C csub(C a, C b) {
+  if constexpr (PK && std::is_same<C, float2>::value) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  else return a - b;
 }
 
-template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+template <typename C, bool PK = true> __device__ __forceinline__ void dft2(C& a, C& b) {
   const C t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+  a = cadd<PK>(t, b);
+  b = csub<PK>(t, b);
 }
-template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
-  const C s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
-  v0 = cadd(s02, s13);
-  v2 = csub(s02, s13);
+template <typename C, bool PK = true> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C s02 = cadd<PK>(v0, v2), d02 = csub<PK>(v0, v2), s13 = cadd<PK>(v1, v3), d13 = csub<PK>(v1, v3);
+  v0 = cadd<PK>(s02, s13);
+  v2 = csub<PK>(s02, s13);
   v1 = d02 + mul_mi(d13);
   v3 = d02 - mul_mi(d13);
 }
@@ -198,17 +202,17 @@ template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, 
 #define GPE_C8 0.92387953251128675613
 #define GPE_S8 0.38268343236508977173
 #define GPE_R2 0.70710678118654752440
-template <typename C> __device__ __forceinline__ void dft8(C* v) {
+template <typename C, bool PK = true> __device__ __forceinline__ void dft8(C* v) {
   C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-  dft4(e0, e1, e2, e3);
-  dft4(o0, o1, o2, o3);
+  dft4<C, PK>(e0, e1, e2, e3);
+  dft4<C, PK>(o0, o1, o2, o3);
   o1 = cmulc(o1, GPE_R2, -GPE_R2);
   o2 = mul_mi(o2);
   o3 = cmulc(o3, -GPE_R2, -GPE_R2);
-  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[0] = cadd<PK>(e0, o0); v[4] = csub<PK>(e0, o0);
+  v[1] = cadd<PK>(e1, o1); v[5] = csub<PK>(e1, o1);
   v[2] = e2 + o2; v[6] = e2 - o2;
-  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+  v[3] = cadd<PK>(e3, o3); v[7] = csub<PK>(e3, o3);
 }
 template <typename C> __device__ __forceinline__ void dft16(C* v) {
   C e[8], o[8];
@@ -228,8 +232,8 @@ template <typename C> __device__ __forceinline__ void dft16(C* v) {
   o[7] = cmulc(o[7], -GPE_C8, -GPE_S8);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    v[i] = cadd(e[i], o[i]);
-    v[i + 8] = csub(e[i], o[i]);
+    v[i] = cadd<true>(e[i], o[i]);
+    v[i + 8] = csub<true>(e[i], o[i]);
   }
 }
 template <typename C, int R> __device__ __forceinline__ void dft_r(C* v) {
