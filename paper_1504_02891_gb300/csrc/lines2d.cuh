@@ -39,7 +39,7 @@ struct LineFFT {
   static constexpr int TPL = F / 8;                 // threads per line
   static constexpr int N8 = LF / 3;                 // radix-8 stages
   static constexpr int TAIL = LF % 3;               // 1: radix-2 tail stage, 2: radix-4 tail stage
-  // line pitch of the exchange buffers (complex): room for pidx(F - 1), and
+  // line pitch of the exchange buffers (complex): room for F points, and
   // = 8 (mod 16) so that neighbouring lines start half a bank row apart
   static constexpr int P = ((F + F / 16 + 15) & ~15) + 8;
   // twiddles e^{-2 pi i n / F} come from the table tws (shared memory); in
@@ -149,13 +149,23 @@ struct LineFFT {
   }
 };
 
-// Exchange slots of a line stored contiguously (row pitch P, padded index):
+// Slot of point m in a line's exchange row: bits 3-6 of m XORed into bits 0-3,
+// a bijection within each 128-point block.  A radix-8 stage with sub-length
+// Ns stores thread j's eight points at 8(j - j mod Ns) + j mod Ns + r Ns, and
+// the next stage loads the points j + s F/8; with this swizzle every such warp
+// access touches the minimum number of shared-memory wavefronts for 8- and
+// 16-byte complex values (checked by enumerating the banks of every warp
+// access for F = 64 ... 1024), where padding one slot per 16 points leaves the
+// stores of the Ns = 8 stage two-way conflicted.
+__device__ __forceinline__ int lidx(int m) { return m ^ ((m >> 3) & 15); }
+
+// Exchange slots of a line stored contiguously (row pitch P, swizzled index):
 // the x-kernel, where the threads of a warp share a line.
 template <typename C, int P>
 struct ExRow {
   C* base;          // line row in buffer 0
   int pstride;      // buffer 1 - buffer 0
-  __device__ __forceinline__ C* operator()(int par, int m) const { return base + par * pstride + pidx(m); }
+  __device__ __forceinline__ C* operator()(int par, int m) const { return base + par * pstride + lidx(m); }
 };
 
 // Exchange slots of CW lines stored interleaved (point-major, the CW lines of
