@@ -48,7 +48,7 @@ ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5
 # DRAM bytes (read + write) of one H psi apply of the happly workload, from the
 # ncu capture summarised in profiles/happly_64x512sq_c64_lines.txt (k_lines_y
 # 227.6 MB + k_lines_x 373.9 MB); must be re-taken whenever those kernels change.
-HAPPLY_DRAM_BYTES_PER_APPLY = 601.5e6
+HAPPLY_DRAM_BYTES_PER_APPLY = 602.8e6
 
 
 def parse():
@@ -246,12 +246,31 @@ def happly_throughput(G, torch, W, peaks, reps=20):
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # Hessian-vector product (Lemma 3.1) on the same batch: read psi and d, write the result
+    d = plan.empty()
+    d.real.normal_()
+    d.imag.normal_()
+    for _ in range(3):
+        plan.hessvec(psi, d, 0.5, out)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        plan.hessvec(psi, d, 0.5, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_h = e0.elapsed_time(e1) / reps
     M = plan.M * nb
     alg = 16.0 * M                 # read psi (8 B) + write H psi (8 B) per point, complex64
     achieved = alg / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
+    alg_h = 24.0 * M               # read psi, d (8 B each) + write (8 B) per point, complex64
     plan.close()
+    hess = {"bound": "hbm", "achieved": alg_h / (ms_h * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg_h / (ms_h * 1e-3) / 1e9 / peak, "traffic": None,
+            "kernel": "Hessian-vector product (gpe_hessvec) = k_lines_y + k_lines_x, same batch",
+            "us_per_apply": ms_h * 1e3, "alg_bytes_per_apply": alg_h}
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "hessvec": hess,
             "traffic": HAPPLY_DRAM_BYTES_PER_APPLY,
             "kernel": "H psi apply = k_lines_y + k_lines_x (register-FFT line kernels), "
                       "64 x 512^2 complex64 rotating (Omega=0.9), float32",
