@@ -106,7 +106,7 @@ struct LineFFT {
         const int mb = ((j - k) << 3) + k;
 #pragma unroll
         for (int r = 0; r < 8; ++r) *ex(par, mb + r * Ns) = v[r];
-        __syncthreads();
+        ex.sync();
 #pragma unroll
         for (int s = 0; s < 8; ++s) v[s] = *ex(par, j + s * TPL);
         par ^= 1;
@@ -160,12 +160,20 @@ struct LineFFT {
 __device__ __forceinline__ int lidx(int m) { return m ^ ((m >> 3) & 15); }
 
 // Exchange slots of a line stored contiguously (row pitch P, swizzled index):
-// the x-kernel, where the threads of a warp share a line.
+// the x-kernel, where the threads of a warp share a line.  Only the line's own
+// threads touch its rows, so an exchange waits for them alone: a named
+// barrier over the line's warps, or the warp itself when a line fits in one.
 template <typename C, int P>
 struct ExRow {
   C* base;          // line row in buffer 0
   int pstride;      // buffer 1 - buffer 0
+  int bar_id;       // named barrier of the line (1 + line in the CTA)
+  int bar_n;        // threads of the line
   __device__ __forceinline__ C* operator()(int par, int m) const { return base + par * pstride + lidx(m); }
+  __device__ __forceinline__ void sync() const {
+    if (bar_n <= 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;\n" ::"r"(bar_id), "r"(bar_n) : "memory");
+  }
 };
 
 // Exchange slots of CW lines stored interleaved (point-major, the CW lines of
@@ -182,6 +190,8 @@ struct ExCols {
     const int ms = m ^ ((m >> 3) & MASK);
     return base + par * pstride + ms * CW;
   }
+  // a column's points are spread over all warps of the CTA
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 // The line symbol: c2 lam^2 + c1 coord lam, lam = dlam * (m or m - F).
@@ -348,7 +358,10 @@ __global__ void __launch_bounds__(LINES_THREADS, 2) k_lines_x(PassGeom<T> G, Pas
   LineSym<T, F> sym;
   sym.c2 = G.c2;
   sym.dl = G.dlam;
-  ExRow<C, FFT::P> ex{xb + l * FFT::P, NL * FFT::P};
+  // lines of F >= 256 points occupy whole warps (TPL >= 32 threads); the
+  // CTA's NL <= 8 lines take named barriers 1..NL
+  static_assert(TPL < 32 || (TPL % 32 == 0 && NL <= 15), "named barriers per line");
+  ExRow<C, FFT::P> ex{xb + l * FFT::P, NL * FFT::P, 1 + l, TPL};
   // element of value q (q = s, or s + 8 for the second row of a real pair)
   auto gidx = [&](int grp, int q) -> long long {
     const int line = grp * NL + l;
@@ -365,8 +378,9 @@ __global__ void __launch_bounds__(LINES_THREADS, 2) k_lines_x(PassGeom<T> G, Pas
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   for (int grp = tile; grp < groups; grp += tiles_per_inst) {
-    // the previous group's reads of ea/ev are done before they are refilled
-    __syncthreads();
+    // the prefetch slots are per thread; the line's exchange rows are reused
+    // by the next group only after the line's own barrier
+    ex.sync();
     const bool more = grp + tiles_per_inst < groups;
     if (more) fetch_x(grp + tiles_per_inst, b ^ 1);
 #pragma unroll
