@@ -48,7 +48,7 @@ ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5
 # DRAM bytes (read + write) of one H psi apply of the happly workload, from the
 # ncu capture summarised in profiles/happly_64x512sq_c64_lines.txt (k_lines_y
 # 227.6 MB + k_lines_x 373.9 MB); must be re-taken whenever those kernels change.
-HAPPLY_DRAM_BYTES_PER_APPLY = 602.8e6
+HAPPLY_DRAM_BYTES_PER_APPLY = 601.2e6
 
 
 def parse():
