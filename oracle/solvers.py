@@ -2,8 +2,7 @@
 
 TEST INFRASTRUCTURE (see package docstring).
 
-Constants the paper leaves open, and the readings taken (all recorded in
-DESIGN.md):
+Constants the paper leaves open, and the readings taken:
   * first step tau = 1e-3; BB alternates tau^{k,1} (even k) / tau^{k,2}
     (odd k), clamped to [1e-20, 1e20] (§3.1 Eq. bb-1, "reset to a finite
     number"); the real inner product Re<S, W> is used for complex data.

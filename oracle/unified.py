@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE (see package docstring).
 
-Rescaling (the paper says only "via a proper rescaling"; reading recorded in
-the design doc): X = sqrt(h_vol) * psi, A = 2 * H_lin, alpha = beta / (2 h_vol), so
+Rescaling (the paper says only "via a proper rescaling"; the reading taken):
+X = sqrt(h_vol) * psi, A = 2 * H_lin, alpha = beta / (2 h_vol), so
 that F(X) = 1/2 X^* A X + alpha sum |X_j|^4 equals E_h(psi), ||X||_2 = ||psi||_h,
 grad F = 2 sqrt(h_vol) H(psi) psi and theta = X^* G = 2 mu_h.
 
