@@ -122,6 +122,27 @@ def test_rotation_sign_from_lz_eigenfunctions():
         assert abs(O.energy(g, f) - lam) < 1e-12
 
 
+def test_rotation_in_3d_acts_in_xy_planes():
+    """3D Fourier grid with trap (1, 1, gamma_z) and -Omega L_z: the rotation
+    acts in every z-plane, so (x +- iy) e^{-(x^2+y^2)/2} e^{-gamma_z z^2/2} is
+    an eigenfunction with eigenvalue (2 + gamma_z)/2 + 1 -+ Omega and the
+    ground Gaussian keeps (2 + gamma_z)/2; a z-odd state z e^{...} is not
+    rotated (eigenvalue (2 + gamma_z)/2 + gamma_z)."""
+    om, gz = 0.6, 2.0
+    p = W.problem(3, (48, 48, 64), (-8.0,) * 3, (8.0,) * 3, "fourier", omega=om, is_complex=True,
+                  potential={"kind": "harmonic", "gamma": (1.0, 1.0, gz)})
+    g = O.build_grid(p)
+    x, y, z = g.mesh(0), g.mesh(1), g.mesh(2)
+    pa = np.exp(-(x * x + y * y) / 2 - gz * z * z / 2) + 0j
+    e0 = (2.0 + gz) / 2.0
+    for f, lam in ((pa, e0), ((x + 1j * y) * pa, e0 + 1.0 - om), ((x - 1j * y) * pa, e0 + 1.0 + om),
+                   (z * pa, e0 + gz)):
+        f = np.broadcast_to(f, g.shape)
+        assert np.max(np.abs(O.apply_hlin(g, f) - lam * f)) < 1e-10, lam
+        f = f / math.sqrt(O.norm2(g, f))
+        assert abs(O.energy(g, f) - lam) < 1e-10
+
+
 def test_fd_second_order():
     """§2.1: the FD operator is second-order accurate (error ratio ~4 per halving)."""
     errs = []
