@@ -90,6 +90,7 @@ static gpe_status tune_lines(gpe_plan p, std::string& rep) {
   // finite data: bytes 0x3c give float32 0.0115 and float64 1.6e-19 everywhere
   cudaMemsetAsync(x, 0x3c, bytes, p->stream);
   const int n0 = g.ext[0], n1 = g.ext[1], nb = g.nbatch, c = g.is_complex, pr = f64 ? 1 : 0;
+  const int wx0 = tuned_waves(0, pr, c, n0, n1, nb), wy0 = tuned_waves(1, pr, c, n0, n1, nb);
   const int cand[4] = {1, 2, 4, 8};
   int wx = 4, wy = 4;
   float best = 1e30f, t = 0.f;
@@ -109,7 +110,10 @@ static gpe_status tune_lines(gpe_plan p, std::string& rep) {
   cudaStreamSynchronize(p->stream);
   cudaFree(x);
   cudaFree(y);
-  if (s != GPE_OK) return s;
+  if (s != GPE_OK) {
+    set_tuned_waves(pr, c, n0, n1, nb, wx0, wy0);   // leave the table as it was
+    return s;
+  }
   set_tuned_waves(pr, c, n0, n1, nb, wx, wy);
   char buf[160];
   snprintf(buf, sizeof(buf), "lines %s%s %dx%d nbatch %d: waves x %d y %d (%.1f us/apply); ", f64 ? "f64" : "f32",
