@@ -56,21 +56,30 @@ def test_largest_grids_operator_parity(name, p, prec):
 
 
 def test_benchmark_happly_configuration_parity():
-    """The timed H-apply: 64 x 512^2 complex64 (Omega = 0.9, beta = 1000) after
-    gpe_plan_autotune; instances 0, 31 and 63 against the oracle, and the
-    whole batch bit for bit against the untuned launch shapes."""
+    """The timed H-apply and Hessian-vector product: 64 x 512^2 complex64
+    (Omega = 0.9, beta = 1000) after gpe_plan_autotune; instances 0, 31 and 63
+    against the oracle, and the H-apply of the whole batch bit for bit against
+    the untuned launch shapes."""
     p = W.config("c4")
     g = O.build_grid(p)
     gen = torch.Generator().manual_seed(1504)
+    shift = 0.5
     with G.Plan(p, nbatch=64, prec=G.F32) as plan:
         host = torch.randn((64,) + plan.shape, dtype=torch.complex64, generator=gen) * 1e-2
+        hd = torch.randn((64,) + plan.shape, dtype=torch.complex64, generator=gen)
         psi = host.cuda()
         out0 = plan.grad(psi)
         plan.autotune()
         out1 = plan.grad(psi)
+        hv = plan.hessvec(psi, hd.cuda(), shift)
         torch.cuda.synchronize()
         assert torch.equal(out0, out1)
         got = out1.cpu().numpy()
+        goth = hv.cpu().numpy()
     for b in (0, 31, 63):
         x = host[b].numpy().astype(np.complex128)
+        d = hd[b].numpy().astype(np.complex128)
         assert rel(got[b].astype(np.complex128), oracle_hpsi(g, x)) <= TOL[G.F32], b
+        refh = (O.apply_hlin(g, d) + g.beta * (np.abs(x) ** 2 * d + 2.0 * np.real(np.conj(x) * d) * x)
+                + shift * d)
+        assert rel(goth[b].astype(np.complex128), refh) <= TOL[G.F32], b
