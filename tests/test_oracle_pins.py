@@ -463,6 +463,22 @@ def test_certificate_complex_data_exclude_the_phase_mode():
     assert abs(lam[1] - lam[0] - 1.0) < 1e-4     # grid accuracy at h = 0.75
 
 
+def test_certificate_3d_rotating_beta0_is_the_eigen_gap():
+    """3D, rotating (Omega = 0.5), trap (1, 1, 2), beta = 0, complex data: on
+    T_X the certificate is 2 (lambda_1 - lambda_0) of the explicit Hermitian
+    H_lin of the same grid (numpy eigh), at the ground state; at the first
+    excited state it is 2 (lambda_0 - lambda_1)."""
+    p = W.problem(3, (8, 8, 8), (-5.0,) * 3, (5.0,) * 3, "fourier", beta=0.0, omega=0.5, is_complex=True,
+                  potential={"kind": "harmonic", "gamma": (1.0, 1.0, 2.0)})
+    g = O.build_grid(p)
+    lam, vec = np.linalg.eigh(_dense_hlin(g))
+    assert lam[1] - lam[0] > 1e-3                 # a simple ground state
+    c0, _ = O.tangent_hessian_min(g, vec[:, 0].reshape(g.shape))
+    c1, _ = O.tangent_hessian_min(g, vec[:, 1].reshape(g.shape))
+    assert abs(c0 - 2.0 * (lam[1] - lam[0])) < 1e-9
+    assert abs(c1 - 2.0 * (lam[0] - lam[1])) < 1e-9
+
+
 def test_certificate_is_a_minimum_over_random_tangent_directions():
     """beta > 0 ground state (oracle solve): no random tangent direction has a
     smaller Rayleigh quotient of grad^2 F - theta than the certificate, and the
