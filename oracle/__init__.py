@@ -19,7 +19,7 @@ from .discretize import (Grid, build_grid, potential, apply_kinetic, apply_hlin,
                          energy, energy_parseval, chem_potential, norm2, rms)
 from .unified import (Unified, cayley_step, cayley_dense, proj_grad)
 from .solvers import (feasible_gradient, armijo_gradient, regularized_newton, prolong, inject,
-                      cascadic, SolveResult)
+                      cascadic, SolveResult, rn_model, rn_ratio_terms, quartic_diff)
 from .certificate import tangent_hessian_min
 
 __all__ = [
@@ -27,4 +27,5 @@ __all__ = [
     "energy_parseval", "chem_potential", "norm2", "rms", "Unified", "cayley_step",
     "cayley_dense", "proj_grad", "feasible_gradient", "armijo_gradient", "regularized_newton",
     "prolong", "inject", "cascadic", "SolveResult", "tangent_hessian_min",
+    "rn_model", "rn_ratio_terms", "quartic_diff",
 ]

@@ -27,7 +27,12 @@ Constants the paper leaves open, and the readings taken:
   * Monotone Armijo search (Remark after Theorem 3.4): delta = 1/2, at most
     60 halvings, alpha_hat given by the caller.
 
-Pins: the monotone search reaches the beta = 0 dense eigenvalue and every
+Pins: rn_ratio_terms (ared, pred) equals F(Z) - F(X^k) and W(Z) - W(X^k)
+evaluated in exact rational arithmetic from Eq. prob and the model's
+definition, for ||D|| down to 1e-6, real and rotating complex data;
+quartic_diff equals sum |X+D|^4 - |X|^4 exactly; rn_model's gradient is the
+derivative of its value (central differences, exact for a quadratic) and
+equals grad F at X^k; the monotone search reaches the beta = 0 dense eigenvalue and every
 step it takes is the Armijo point (the step before it fails Eq. Armijo1);
 Algorithm 1/2 reach the beta = 0 ground-state energy (closed form d/2,
 and the smallest eigenvalue of the dense operator on tiny grids), the printed
@@ -160,11 +165,62 @@ def armijo_gradient(fg, X0, *, alpha_hat=1.0, rho1=1e-4, delta_bt=0.5, max_bt=60
     return SolveResult(X, F, k, nfe, math.sqrt(inner(P, P)), hist)
 
 
-def _quartic_diff(X, D):
-    """sum |X+D|^4 - |X|^4 written as sum (2 Re(conj X D) + |D|^2)(|X+D|^2 + |X|^2)."""
+def quartic_diff(X, D):
+    """sum |X+D|^4 - sum |X|^4, written per point as a difference of squares:
+    |X+D|^4 - |X|^4 = (|X+D|^2 - |X|^2)(|X+D|^2 + |X|^2) with
+    |X+D|^2 - |X|^2 = 2 Re(conj(X) D) + |D|^2, so that no two large terms
+    cancel when D is small."""
     x2 = np.abs(X) ** 2
     z2 = np.abs(X + D) ** 2
     return float(np.sum((2.0 * np.real(np.conj(X) * D) + np.abs(D) ** 2) * (z2 + x2)))
+
+
+def rn_model(U: Unified, Xk, delta):
+    """The model of §3.2 at X^k as a function of Z, with its gradient:
+    W(Z) = 1/2 Z^*AZ + 4 alpha sum |X^k|^2 R + 2 alpha sum (|X^k|^2 |D|^2 + 2 R^2)
+           + delta/2 ||D||^2,   D = Z - X^k,  R = Re(conj(X^k) D)
+    (Eq. mL with delta taken outside the alpha term, as in the model W-tilde
+    that precedes it), and
+    grad W(Z) = AZ + 4 alpha |X^k|^2 Z + 8 alpha R X^k + delta D
+    (the printed gradient, with delta for the printed tau).  Returns
+    wg(Z) -> (W(Z), grad W(Z))."""
+    alpha = U.alpha
+    x2 = np.abs(Xk) ** 2
+
+    def wg(Z):
+        D = Z - Xk
+        AZ = U.A(Z)
+        R = np.real(np.conj(Xk) * D)
+        W = (0.5 * inner(Z, AZ) + 4.0 * alpha * float(np.sum(x2 * R))
+             + 2.0 * alpha * float(np.sum(x2 * np.abs(D) ** 2 + 2.0 * R * R))
+             + 0.5 * delta * inner(D, D))
+        gW = AZ + 4.0 * alpha * x2 * Z + 8.0 * alpha * R * Xk + delta * D
+        return W, gW
+
+    return wg
+
+
+def rn_ratio_terms(U: Unified, Xk, Gk, Z, delta):
+    """Numerator and denominator of Eq. TR-ratio for the trial point Z:
+        ared = F(Z) - F(X^k),   pred = W(Z) - W(X^k),
+    each written as a sum of terms in D = Z - X^k (no difference of two
+    objective values, which would cancel near convergence):
+        ared = Re<A X^k, D> + 1/2 D^*AD + alpha (sum |X^k+D|^4 - |X^k|^4)
+        pred = Re<G_k, D> + 1/2 grad^2 F(X^k)[D, D] + delta/2 ||D||^2
+    with A X^k = G_k - 4 alpha |X^k|^2 X^k (Lemma 3.1) and grad^2 F[D, D] as
+    printed in Lemma 3.1.  Both are algebraically identical to the plain
+    differences."""
+    alpha = U.alpha
+    x2 = np.abs(Xk) ** 2
+    D = Z - Xk
+    AD = U.A(D)
+    AX = Gk - 4.0 * alpha * x2 * Xk
+    dAd = inner(D, AD)
+    R = np.real(np.conj(Xk) * D)
+    ared = inner(AX, D) + 0.5 * dAd + alpha * quartic_diff(Xk, D)
+    hq = dAd + 4.0 * alpha * float(np.sum(x2 * np.abs(D) ** 2 + 2.0 * R * R))
+    pred = inner(Gk, D) + 0.5 * hq + 0.5 * delta * inner(D, D)
+    return ared, pred
 
 
 def regularized_newton(U: Unified, X0, *, k_init=100, k_sub=200, delta0=1.0,
@@ -185,39 +241,20 @@ def regularized_newton(U: Unified, X0, *, k_init=100, k_sub=200, delta0=1.0,
     delta = delta0
     hist = []
     outer = 0
-    alpha = U.alpha
     while outer < max_outer:
         P = proj_grad(X, G)
         pn = math.sqrt(inner(P, P))
         if res_tol > 0.0 and pn <= res_tol:
             break
         Xk, Gk = X, G
-        x2 = np.abs(Xk) ** 2
-
-        def wg(Z, Xk=Xk, Gk=Gk, x2=x2, delta=delta):
-            # W^(k)(Z) of §3.2 (delta outside the alpha term) and its gradient.
-            D = Z - Xk
-            AZ = U.A(Z)
-            R = np.real(np.conj(Xk) * D)
-            W = (0.5 * inner(Z, AZ) + 4.0 * alpha * float(np.sum(x2 * R))
-                 + 2.0 * alpha * float(np.sum(x2 * np.abs(D) ** 2 + 2.0 * R * R))
-                 + 0.5 * delta * inner(D, D))
-            gW = AZ + 4.0 * alpha * x2 * Z + 8.0 * alpha * R * Xk + delta * D
-            return W, gW
-
+        wg = rn_model(U, Xk, delta)
         sub = feasible_gradient(wg, Xk, max_iter=k_sub, eps0=0.0,
                                 res_tol=max(sub_rel * pn, 1e-14))
         nfe += sub.nfe
         inner_total += sub.iters
         Z = sub.X
         D = Z - Xk
-        AD = U.A(D)
-        AX = Gk - 4.0 * alpha * x2 * Xk
-        dAd = inner(D, AD)
-        R = np.real(np.conj(Xk) * D)
-        ared = inner(AX, D) + 0.5 * dAd + alpha * _quartic_diff(Xk, D)
-        hq = dAd + 4.0 * alpha * float(np.sum(x2 * np.abs(D) ** 2 + 2.0 * R * R))
-        pred = inner(Gk, D) + 0.5 * hq + 0.5 * delta * inner(D, D)
+        ared, pred = rn_ratio_terms(U, Xk, Gk, Z, delta)
         if abs(pred) <= 1e-15 * max(abs(F), 1.0):
             rho = 1.0
         else:

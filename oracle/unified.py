@@ -82,16 +82,32 @@ def proj_grad(X, G):
 
 
 def cayley_step(X, G, tau):
-    """Y(tau) = a(tau) X + b(tau) G with Theorem 3.3's coefficients.
+    """Y(tau) = a(tau) X + b(tau) G with Theorem 3.3's coefficients, as printed:
+        a = ((1 + tau X^*G)^2 - tau^2 ||X||^2 ||G||^2) / den,
+        b = -2 tau ||X||^2 / den,
+        den = 1 - tau^2 (X^*G)^2 + tau^2 ||X||^2 ||G||^2.
 
     X^* G is real for Hermitian A (the tangent-space reading for complex data);
     its real part is used.
+
+    Guarded fallback: the printed expressions contain
+    c = ||X||^2 ||G||^2 - (X^*G)^2 >= 0 (Cauchy-Schwarz) as a difference of two
+    nearly equal numbers once G is almost parallel to X (near a stationary
+    point c ~ ||A(X)X||^2 while ||X||^2 ||G||^2 ~ (2 mu)^2).  When more than
+    half of the digits of c cancel, c is taken instead as
+    ||X||^2 |G - (X^*G / ||X||^2) X|^2, the same number by Pythagoras, which
+    cannot come out negative; the coefficients are then the printed ones with
+    this value of c.
     """
     xg = float(np.real(np.vdot(X, G)))
     nx = float(np.real(np.vdot(X, X)))
-    # (X^*X)(G^*G) - (X^*G)^2 >= 0 (Cauchy-Schwarz), evaluated as
-    # (X^*X) |G - (X^*G / X^*X) X|^2 so that rounding cannot make it negative
-    # and the denominator 1 + tau^2 (...) of Theorem 3.3 stays >= 1 for any tau.
+    ng = float(np.real(np.vdot(G, G)))
+    if nx * ng - xg * xg > 1e-8 * nx * ng:
+        # the printed form
+        den = 1.0 - tau * tau * xg * xg + tau * tau * nx * ng
+        a = ((1.0 + tau * xg) ** 2 - tau * tau * nx * ng) / den
+        b = -2.0 * tau * nx / den
+        return a * X + b * G
     P = G - (xg / nx) * X
     cs = nx * float(np.real(np.vdot(P, P)))
     den = 1.0 + tau * tau * cs

@@ -281,6 +281,14 @@ def test_cayley_closed_form_vs_dense_solve(cplx):
     dY = (O.cayley_step(X, G, t) - O.cayley_step(X, G, -t)) / (2 * t)
     assert np.max(np.abs(dY + 2 * O.proj_grad(X, G))) < 1e-6 * np.max(np.abs(G))
     del omega
+    # near a stationary point (G almost parallel to X) the printed coefficients
+    # lose their digits and the guarded form is taken: still the dense solution
+    Gs = 7.0 * X + 1e-7 * (G - inner(X, G) * X)
+    for tau in (1e-3, 0.05, 0.7, 30.0):
+        Y = O.cayley_step(X, Gs, tau)
+        Yd = O.cayley_dense(X, Gs, tau)
+        assert np.max(np.abs(Y - Yd)) < 1e-12
+        assert abs(np.linalg.norm(Y) - 1.0) < 1e-13
 
 
 def test_ratio_model_second_order():
@@ -296,6 +304,168 @@ def test_ratio_model_second_order():
         model = inner(G, Dd) + 0.5 * U.hess_quad(X, Dd)
         errs.append(abs(ared - model))
     assert 6.0 < errs[0] / errs[1] < 10.0 and 6.0 < errs[1] / errs[2] < 10.0
+    # the same through the oracle's ratio terms (delta = 0.3): rho -> 1
+    rhos = []
+    for s in (1e-2, 1e-3, 1e-4):
+        ared, pred = O.rn_ratio_terms(U, X, G, X + s * D, 0.3)
+        rhos.append(ared / (pred - 0.15 * s * s * inner(D, D)))
+    assert abs(rhos[2] - 1.0) < 1e-3 and abs(rhos[2] - 1.0) < abs(rhos[0] - 1.0)
+
+
+# Exact arithmetic for the ratio-test pins: every float64 number is a dyadic
+# rational, so with the operator written as the explicit real matrix of
+# X -> A X (its columns are A applied to unit vectors) the objective and the
+# model can be evaluated without rounding in fractions.Fraction.
+
+def _real_vec(X):
+    X = np.asarray(X)
+    if np.iscomplexobj(X):
+        return np.concatenate([X.real.ravel(), X.imag.ravel()])
+    return X.ravel().astype(np.float64)
+
+
+def _op_matrix(U, shape, cplx):
+    """Real matrix Ahat with Re<X, A Y> = r(X) . Ahat r(Y), r = _real_vec."""
+    M = int(np.prod(shape))
+    cols = []
+    for k in range(M):
+        e = np.zeros(M)
+        e[k] = 1.0
+        cols.append(_real_vec(U.A(e.reshape(shape) + (0j if cplx else 0.0))))
+    if cplx:
+        for k in range(M):
+            e = np.zeros(M, dtype=np.complex128)
+            e[k] = 1j
+            cols.append(_real_vec(U.A(e.reshape(shape))))
+    return np.array(cols).T
+
+
+def _fr(v):
+    from fractions import Fraction
+    return [Fraction(float(t)) for t in v]
+
+
+def _exact_quad(Ah, x, y):
+    """x . Ahat y in exact arithmetic (x, y lists of Fractions)."""
+    from fractions import Fraction
+    tot = Fraction(0)
+    for i, xi in enumerate(x):
+        if xi == 0:
+            continue
+        row = Ah[i]
+        acc = Fraction(0)
+        for j, yj in enumerate(y):
+            if yj != 0 and row[j] != 0.0:
+                acc += Fraction(float(row[j])) * yj
+        tot += xi * acc
+    return tot
+
+
+def _exact_abs2(x, M, cplx):
+    """|X_j|^2 per point from the real vector (exact)."""
+    if cplx:
+        return [x[j] * x[j] + x[M + j] * x[M + j] for j in range(M)]
+    return [x[j] * x[j] for j in range(M)]
+
+
+def _ratio_case(cplx, seed):
+    omega = 0.7 if cplx else 0.0
+    p = W.problem(2, (8, 8), (-3.0, -3.0), (3.0, 3.0), "fourier", beta=40.0, omega=omega, is_complex=cplx)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal(g.shape) + (1j * rng.standard_normal(g.shape) if cplx else 0.0)
+    X = X / np.linalg.norm(X)
+    E = rng.standard_normal(g.shape) + (1j * rng.standard_normal(g.shape) if cplx else 0.0)
+    E = E / np.linalg.norm(E)
+    return g, U, X, E
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex_rotating"])
+def test_ratio_terms_equal_exact_differences(cplx):
+    """Eq. TR-ratio: the oracle's difference-form numerator and denominator
+    (rn_ratio_terms) equal F(Z) - F(X^k) and W(Z) - W(X^k), W the model of §3.2
+    written out from its definition, evaluated here in exact rational
+    arithmetic, for ||D|| = 1e-1, 1e-3, 1e-6 (beta > 0; Omega > 0 for complex
+    data).  A wrong factor or sign in any term of either expression changes the
+    value at first or second order in D and fails at every size."""
+    from fractions import Fraction
+    g, U, X, E = _ratio_case(cplx, 11)
+    M = X.size
+    Ah = _op_matrix(U, g.shape, cplx)
+    alpha = Fraction(float(U.alpha))
+    Gk = U.grad(X)
+    x = _fr(_real_vec(X))
+    ax = _exact_quad(Ah, x, x)
+    x2 = _exact_abs2(x, M, cplx)
+    for size in (1e-1, 1e-3, 1e-6):
+        delta = 0.37
+        D = size * E
+        Z = X + D
+        ared, pred = O.rn_ratio_terms(U, X, Gk, Z, delta)
+        # the floats actually used: D is Z - X^k as the oracle forms it
+        d = _fr(_real_vec(Z - X))
+        z = [a + b for a, b in zip(x, d)]
+        z2 = _exact_abs2(z, M, cplx)
+        d2 = _exact_abs2(d, M, cplx)
+        # F(Z) - F(X) from Eq. prob
+        F_diff = (_exact_quad(Ah, z, z) - ax) / 2 + alpha * sum(a * a - b * b for a, b in zip(z2, x2))
+        # W(Z) - W(X^k) from the model's definition (W(X^k) = X^k*AX^k / 2)
+        if cplx:
+            R = [x[j] * d[j] + x[M + j] * d[M + j] for j in range(M)]
+        else:
+            R = [x[j] * d[j] for j in range(M)]
+        Wz = (_exact_quad(Ah, z, z) / 2 + 4 * alpha * sum(a * r for a, r in zip(x2, R))
+              + 2 * alpha * sum(a * b + 2 * r * r for a, b, r in zip(x2, d2, R))
+              + Fraction(delta) / 2 * sum(d2))
+        W_diff = Wz - ax / 2
+        # rounding scale of the float evaluation: size of its terms
+        scale = size * float(np.linalg.norm(Gk)) + size * size * float(np.linalg.norm(Ah, 2))
+        assert abs(ared - float(F_diff)) <= 1e-13 * scale, (size, ared, float(F_diff))
+        assert abs(pred - float(W_diff)) <= 1e-13 * scale, (size, pred, float(W_diff))
+        # the plain float difference cancels at small D; the difference form does not
+        if size == 1e-6:
+            assert abs(float(F_diff)) > 1e-9
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex"])
+def test_quartic_diff_exact(cplx):
+    """sum |X+D|^4 - sum |X|^4 (the quartic part of ared), against exact
+    rational arithmetic, for ||D|| from 1e-1 to 1e-8."""
+    g, U, X, E = _ratio_case(cplx, 12)
+    M = X.size
+    x = _fr(_real_vec(X))
+    x2 = _exact_abs2(x, M, cplx)
+    for size in (1e-1, 1e-4, 1e-8):
+        D = size * E
+        q = O.quartic_diff(X, D)
+        d = _fr(_real_vec(D))
+        z = [a + b for a, b in zip(x, d)]          # X + D without rounding
+        z2 = _exact_abs2(z, M, cplx)
+        exact = float(sum(a * a - b * b for a, b in zip(z2, x2)))
+        assert abs(q - exact) <= 1e-13 * (size * 4 * float(np.sum(np.abs(X) ** 3)) + size * size), (size, q, exact)
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex_rotating"])
+def test_rn_model_gradient_is_its_derivative(cplx):
+    """The model gradient of §3.2 (rn_model) is the derivative of the model
+    value: W is quadratic in Z, so a central difference is exact up to
+    rounding, along random directions and at random points."""
+    g, U, X, E = _ratio_case(cplx, 13)
+    rng = np.random.default_rng(14)
+    wg = O.rn_model(U, X, 0.25)
+    for _ in range(3):
+        Z = X + 0.1 * (rng.standard_normal(g.shape) + (1j * rng.standard_normal(g.shape) if cplx else 0.0))
+        Dir = rng.standard_normal(g.shape) + (1j * rng.standard_normal(g.shape) if cplx else 0.0)
+        eps = 1e-3
+        Wp, _ = wg(Z + eps * Dir)
+        Wm, _ = wg(Z - eps * Dir)
+        _, gW = wg(Z)
+        fd = (Wp - Wm) / (2 * eps)
+        assert abs(fd - inner(gW, Dir)) <= 1e-8 * (abs(fd) + 1.0), (fd, inner(gW, Dir))
+    # at Z = X^k the model gradient is the gradient of F (first-order match)
+    _, g0 = wg(X)
+    assert np.max(np.abs(g0 - U.grad(X))) <= 1e-12 * np.max(np.abs(g0))
 
 
 # ---------------------------------------------------------------- solvers
