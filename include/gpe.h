@@ -263,9 +263,10 @@ gpe_status gpe_autotune_report(char* buf, size_t buflen);
 
 /* Allocation-free Cayley step (the paper has no counterpart: this is a
  * packaging variant of gpe_feasible_step for callers that cannot call
- * cudaMalloc -- e.g. code running inside a stream capture that must stay free
- * of allocation calls, inside an allocator or memory-pool callback, or under a
- * fixed up-front memory budget -- and so cannot create a plan).
+ * cudaMalloc -- e.g. code running inside an allocator or memory-pool callback,
+ * which must not re-enter the allocator, a loop whose device memory budget was
+ * fixed up front, or a host framework that owns all device memory and passes
+ * the library only its own buffers -- and so cannot create a plan).
  * Computes the same result as gpe_feasible_step(..., E_out = NULL) for
  * `nbatch` instances of `n_unknowns` values each: psi and hpsi are device
  * buffers in the layout above (prec = gpe_prec, is_complex as in the problem),
@@ -277,8 +278,10 @@ gpe_status gpe_autotune_report(char* buf, size_t buflen);
  * 1 <= nbatch <= 64 and nbatch * min(ceil(n_unknowns / 256), 512) <= 4096;
  * larger requests return GPE_EINVAL and do nothing.
  * The first call on each device (with that device current) looks up the
- * array's device address with cudaGetSymbolAddress and caches it; make that
- * first call before any stream capture.  Every call reuses the same array, so
+ * array's device address with cudaGetSymbolAddress and caches it with the
+ * identity of the device's CUDA context; the first call after a
+ * cudaDeviceReset (a new context) looks it up again.  Make that first call
+ * before any stream capture.  Every call reuses the same array, so
  * calls whose work overlaps on the GPU (other streams, other threads) race;
  * serialise them.  The call allocates nothing. */
 gpe_status gpe_feasible_step_noalloc(int prec, int is_complex, int64_t n_unknowns, int nbatch, double h_vol,

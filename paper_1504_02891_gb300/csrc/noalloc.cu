@@ -2,18 +2,22 @@
 // gpe_feasible_step for callers that cannot allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is unavailable or forbidden --
-// inside a CUDA stream capture that must not contain allocation calls, inside a
-// custom allocator or memory-pool callback, in a real-time loop whose memory
-// budget was fixed up front, or in a host that gives the library only
-// caller-owned buffers.  gpe_feasible_step needs a plan, and creating a plan
-// allocates tables and reduction scratch; this entry point takes no plan.
+// inside a custom allocator or memory-pool callback (which must not re-enter
+// the allocator), in a real-time loop whose device memory budget was fixed up
+// front, or in a host framework that owns all device memory and hands the
+// library only caller-owned buffers.  gpe_feasible_step needs a plan, and
+// creating a plan allocates tables and reduction scratch; this entry point
+// takes no plan.
 //
 // Where its scratch lives: one file-scope device array (g_noalloc_scratch),
 // 512 KiB, placed in every GPU's memory when the library is loaded on it and
 // kept until the process exits.  Host code cannot use the array's name as a
 // device address (it names a host-side shadow), so the device address is
-// looked up with cudaGetSymbolAddress once per device, on the first call made
-// while that device is current, and cached.
+// looked up with cudaGetSymbolAddress on the first call made while a device is
+// current, and cached together with the identity of that device's CUDA
+// context: after a cudaDeviceReset the context (and the array's address) is
+// new, and the next call looks the address up again.
+#include <cuda.h>
 #include <mutex>
 #include "ops_impl.cuh"
 
@@ -33,7 +37,44 @@ static_assert((NOALLOC_PARTIALS + NOALLOC_RESULTS + NOALLOC_COEF) * sizeof(doubl
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 std::mutex g_mu;
-void* g_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+struct CachedAddr {
+  unsigned long long ctx_id;   // 0: nothing cached
+  void* addr;
+};
+CachedAddr g_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Driver entry points for the identity of the current context, resolved
+// through the runtime (the library does not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+gpe_status resolve_driver_calls() {
+  if (g_ctx_current && g_ctx_id) return GPE_OK;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+  if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1)
+    return gpe::cuda_fail(e != cudaSuccess ? e : cudaErrorSymbolNotFound, "driver entry point cuCtxGetCurrent");
+  e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+  if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2)
+    return gpe::cuda_fail(e != cudaSuccess ? e : cudaErrorSymbolNotFound, "driver entry point cuCtxGetId");
+  g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return GPE_OK;
+}
+
+// Unique id of the context current on this thread (0 if none yet).
+gpe_status current_ctx_id(unsigned long long* id) {
+  *id = 0;
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) return gpe::fail(GPE_ECUDA, "cuCtxGetCurrent failed");
+  if (!ctx) return GPE_OK;
+  if (g_ctx_id(ctx, id) != CUDA_SUCCESS) return gpe::fail(GPE_ECUDA, "cuCtxGetId failed");
+  return GPE_OK;
+}
 
 gpe_status scratch_address(unsigned char** out) {
   int dev = 0;
@@ -41,13 +82,25 @@ gpe_status scratch_address(unsigned char** out) {
   if (e != cudaSuccess) return gpe::cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return gpe::fail(GPE_EINVAL, "device index beyond the supported range");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  gpe_status s = resolve_driver_calls();
+  if (s != GPE_OK) return s;
+  unsigned long long id = 0;
+  s = current_ctx_id(&id);
+  if (s != GPE_OK) return s;
+  CachedAddr& c = g_addr[dev];
+  if (id == 0 || c.ctx_id != id) {
+    // first call on this device, or its context was replaced (device reset):
+    // the lookup also makes the device's primary context current if needed
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return gpe::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_addr[dev] = p;
+    s = current_ctx_id(&id);
+    if (s != GPE_OK) return s;
+    if (id == 0) return gpe::fail(GPE_ECUDA, "no CUDA context current after cudaGetSymbolAddress");
+    c.ctx_id = id;
+    c.addr = p;
   }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  *out = static_cast<unsigned char*>(c.addr);
   return GPE_OK;
 }
 
