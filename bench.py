@@ -227,11 +227,16 @@ AUTOTUNE_ERRORS = []
 
 
 def tune_or_note(G, plan, levels):
-    """gpe_plan_autotune; a failure is recorded in the JSON line and the run
-    continues with the fixed launch rule (the choice never changes results)."""
+    """gpe_plan_autotune; a failure it can recover from (no memory for a
+    candidate shape, a shape the plan rejects) is recorded in the JSON line and
+    the run continues with the fixed launch rule (the choice never changes
+    results).  Any other status -- a CUDA error, an expired device wait -- may
+    leave the context unusable, so it stops the run."""
     try:
         plan.autotune(levels=levels)
     except G.GPEError as e:
+        if getattr(e, "status", None) not in (G.ENOMEM, G.EINVAL):
+            raise
         AUTOTUNE_ERRORS.append(str(e)[:200])
 
 

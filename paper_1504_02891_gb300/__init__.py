@@ -25,6 +25,7 @@ F32, F64 = 0, 1
 V_HARMONIC, V_LATTICE, V_STIRRER, V_ARRAY = 0, 1, 2, 3
 _DISC = {"fourier": FOURIER, "sine": SINE, "fd": FD}
 
+OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, ENOCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6
 STATUS = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_ECUDA", 3: "GPE_ENOMEM",
           4: "GPE_ENONFINITE", 5: "GPE_ENOCONV", 6: "GPE_ETIMEOUT"}
 

@@ -266,7 +266,10 @@ static gpe_status run_chunk(Level<T>& L, int objective, const SolveParams& P, cu
     GPE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     gpe_status s = queue_iters<T>(L, objective, P.chunk, st);
     cudaError_t e = cudaStreamEndCapture(st, &graph);
-    if (s != GPE_OK) return s;
+    if (s != GPE_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(graph);
+      return s;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     size_t nn = 0;
     cudaGraphGetNodes(graph, nullptr, &nn);
