@@ -254,6 +254,8 @@ gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* const* psi,
  * rounding order).  Other grids: nothing to tune, GPE_OK.  Allocates scratch
  * of two plan vectors and one solver level per grid; synchronises.  Not
  * thread-safe with concurrent launches on the tuned shapes.
+ *   - float32 square grids: the fused one-launch operator kernel against the
+ *     two line kernels, for this grid and batch;
  * Errors: GPE_EINVAL (NULL plan, levels outside [1, 8]), GPE_ENOMEM, GPE_ECUDA. */
 gpe_status gpe_plan_autotune(gpe_plan plan, int levels);
 
@@ -299,6 +301,39 @@ gpe_status gpe_feasible_step_noalloc(int prec, int is_complex, int64_t n_unknown
  *   object {"kernel-name": [launches, total_ms], ...} into buf (NUL
  *   terminated, truncated to buflen).  GPE_EINVAL if buf is NULL. */
 int64_t gpe_kernel_launches(void);
+
+/* Operator implementation on float32 square 2D Fourier grids (the paper has
+ * no counterpart: an implementation choice that never changes the operator's
+ * values beyond rounding order).  path 0: automatic -- the choice
+ * gpe_plan_autotune measured for the grid and batch, else the fused kernel
+ * for lines of up to 256 points; 1: always the fused one-launch kernel;
+ * 2: always the two line kernels.  Process-wide, for later launches; a
+ * diagnostic and test knob.  Errors: GPE_EINVAL (path outside 0..2). */
+gpe_status gpe_set_operator_path(int path);
+
+/* Bounded device waits (the paper has no counterpart: failure handling).  The
+ * persistent Algorithm 1 launch waits at grid barriers and the fused 2D
+ * operator kernel's x-tasks wait for the y-tasks of their instance; each wait
+ * polls at most a fixed number of times (2^22 barrier polls, 2^24 task polls,
+ * about a second) and then gives up: gpe_rnewton_solve returns GPE_ETIMEOUT,
+ * and so do gpe_energy and gpe_grad with energies requested (the outputs of
+ * that call are not valid).  gpe_set_wait_limit(n), n > 0, replaces both
+ * limits by n polls for every later launch in this process (a diagnostic
+ * and test knob: a limit of 1 makes a wait give up almost at once); n = 0
+ * restores the defaults.  Not thread-safe with concurrent launches.
+ * Errors: GPE_EINVAL (n < 0). */
+gpe_status gpe_set_wait_limit(int64_t polls);
+
+/* Arithmetic peak of the current device, measured (the paper has no
+ * counterpart: instrumentation for the roofline of the operator kernels).
+ * kind 0: float32 fused multiply-add; 1: packed two-lane float32 multiply-add
+ * (one instruction, two results); 2: float64 fused multiply-add.  Runs six
+ * launches of independent multiply-add chains on every SM at full occupancy
+ * on `stream` (a cudaStream_t, NULL = legacy default stream), times the last
+ * five with CUDA events, synchronises, and writes the rate in TFLOP/s
+ * (2 flops per multiply-add) to *tflops.  Allocates nothing.
+ * Errors: GPE_EINVAL (kind, NULL tflops), GPE_ECUDA. */
+gpe_status gpe_probe_peak(int kind, void* stream, double* tflops);
 gpe_status gpe_profile_enable(int on);
 gpe_status gpe_profile_summary(char* buf, int buflen);
 

@@ -125,6 +125,9 @@ def load():
         "gpe_kernel_launches": ([], C.c_int64),
         "gpe_profile_enable": ([ip], ip),
         "gpe_profile_summary": ([C.c_char_p, ip], ip),
+        "gpe_probe_peak": ([ip, vp, dp], ip),
+        "gpe_set_wait_limit": ([C.c_int64], ip),
+        "gpe_set_operator_path": ([ip], ip),
     }
     missing = [name for name in sig if not hasattr(L, name)]
     if missing:
@@ -337,6 +340,28 @@ def solve_batch(params_list, psis, stream=None, **opts):
 def kernel_launches():
     """Kernels launched through libgpe by this process so far."""
     return int(load().gpe_kernel_launches())
+
+
+def set_operator_path(path=0):
+    """gpe_set_operator_path: 0 automatic, 1 fused 2D kernel, 2 two line kernels."""
+    _check(load().gpe_set_operator_path(int(path)))
+
+
+def set_wait_limit(polls=0):
+    """gpe_set_wait_limit: polls after which a bounded device wait gives up
+    (0 restores the defaults)."""
+    _check(load().gpe_set_wait_limit(int(polls)))
+
+
+def probe_peak(kind, stream=None):
+    """gpe_probe_peak: measured multiply-add rate of the current device in
+    TFLOP/s; kind 0 float32, 1 packed two-lane float32, 2 float64."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = C.c_double()
+    _check(load().gpe_probe_peak(int(kind), C.c_void_p(stream.cuda_stream), C.byref(out)))
+    return float(out.value)
 
 
 def profile_enable(on=True):

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build", "gpe")
 LIB = os.path.join(PKG, "libgpe.so")
-SOURCES = ["ops_f32.cu", "ops_f64.cu", "plan.cu", "solver.cu", "noalloc.cu", "cluster.cu", "lines2d_f32.cu", "lines2d_f64.cu", "certificate.cu", "autotune.cu"]
+SOURCES = ["ops_f32.cu", "ops_f64.cu", "plan.cu", "solver.cu", "noalloc.cu", "cluster.cu", "lines2d_f32.cu", "lines2d_f64.cu", "certificate.cu", "autotune.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -10,7 +10,11 @@
 //     per-CTA share of one state vector (2-32 KiB), which sets the cluster
 //     size (smaller share: more CTAs per instance, shorter line passes, more
 //     cluster-wide synchronisation).
-// Launches with no table entry use the fixed rule (4 waves; 4 KiB).  The
+//   * float32 square 2D Fourier grids: the fused one-launch operator kernel
+//     (fused2d.cuh) or the two line kernels, whichever applies the operator
+//     faster for the grid and batch.
+// Launches with no table entry use the fixed rule (4 waves; 4 KiB; the fused
+// kernel for lines of up to 256 points).  The
 // choice never changes what is computed, only how the work is spread: the
 // operator values are identical, reductions may differ by rounding order.
 #include <map>
@@ -26,7 +30,20 @@ namespace {
 std::mutex g_mu;
 std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_waves;   // (prec, cplx, n0, n1, nbatch)
 std::map<std::tuple<int, int, int>, int> g_share;                            // (n0, n1, cplx)
+std::map<std::tuple<int, int, int>, int> g_fused;                            // (cplx, n, nbatch)
 }  // namespace
+
+bool tuned_fused(int cplx, int n, int nbatch) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_fused.find(std::make_tuple(cplx, n, nbatch));
+  if (it == g_fused.end()) return n <= 256;
+  return it->second != 0;
+}
+
+void set_tuned_fused(int cplx, int n, int nbatch, int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_fused[std::make_tuple(cplx, n, nbatch)] = on;
+}
 
 int tuned_waves(int axis, int prec64, int cplx, int n0, int n1, int nbatch) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -91,6 +108,10 @@ static gpe_status tune_lines(gpe_plan p, std::string& rep) {
   cudaMemsetAsync(x, 0x3c, bytes, p->stream);
   const int n0 = g.ext[0], n1 = g.ext[1], nb = g.nbatch, c = g.is_complex, pr = f64 ? 1 : 0;
   const int wx0 = tuned_waves(0, pr, c, n0, n1, nb), wy0 = tuned_waves(1, pr, c, n0, n1, nb);
+  // the waves are those of the two line kernels: time them, not the fused kernel
+  const bool sq = !f64 && n0 == n1;
+  const bool fused0 = sq && tuned_fused(c, n0, nb);
+  if (sq) set_tuned_fused(c, n0, nb, 0);
   const int cand[4] = {1, 2, 4, 8};
   int wx = 4, wy = 4;
   float best = 1e30f, t = 0.f;
@@ -110,14 +131,55 @@ static gpe_status tune_lines(gpe_plan p, std::string& rep) {
   cudaStreamSynchronize(p->stream);
   cudaFree(x);
   cudaFree(y);
+  if (sq) set_tuned_fused(c, n0, nb, fused0 ? 1 : 0);
   if (s != GPE_OK) {
     set_tuned_waves(pr, c, n0, n1, nb, wx0, wy0);   // leave the table as it was
     return s;
   }
   set_tuned_waves(pr, c, n0, n1, nb, wx, wy);
-  char buf[160];
+  char buf[200];
   snprintf(buf, sizeof(buf), "lines %s%s %dx%d nbatch %d: waves x %d y %d (%.1f us/apply); ", f64 ? "f64" : "f32",
            c ? " complex" : "", n0, n1, nb, wx, wy, best);
+  rep += buf;
+  return GPE_OK;
+}
+
+// Float32 square grids: the fused kernel against the two line kernels (with
+// their tuned waves); the faster is recorded for the grid and batch.
+static gpe_status tune_fused(gpe_plan p, std::string& rep) {
+  const GridHost& g = p->g;
+  if (p->prec != GPE_F32 || g.disc != GPE_FOURIER || g.dim != 2 || g.ext[0] != g.ext[1]) return GPE_OK;
+  const int n = g.ext[0];
+  if (n < 64 || n > 1024 || (n & (n - 1)) != 0 || operator_path() != 0) return GPE_OK;
+  const size_t bytes = 4 * (g.is_complex ? 2 : 1) * (size_t)g.M * g.nbatch;
+  void* x = nullptr;
+  void* y = nullptr;
+  GPE_CUDA(cudaMalloc(&x, bytes));
+  if (cudaMalloc(&y, bytes) != cudaSuccess) {
+    cudaFree(x);
+    return fail(GPE_ENOMEM, "autotune scratch");
+  }
+  cudaMemsetAsync(x, 0x3c, bytes, p->stream);
+  const int c = g.is_complex, nb = g.nbatch;
+  const bool was = tuned_fused(c, n, nb);
+  float t[2] = {0.f, 0.f};
+  gpe_status s = GPE_OK;
+  for (int on = 0; on < 2 && s == GPE_OK; ++on) {
+    set_tuned_fused(c, n, nb, on);
+    s = time_grad(p, x, y, 5, &t[on]);
+  }
+  cudaStreamSynchronize(p->stream);
+  cudaFree(x);
+  cudaFree(y);
+  if (s != GPE_OK) {
+    set_tuned_fused(c, n, nb, was ? 1 : 0);
+    return s;
+  }
+  const int best = t[1] < t[0] ? 1 : 0;
+  set_tuned_fused(c, n, nb, best);
+  char buf[200];
+  snprintf(buf, sizeof(buf), "operator f32%s %dx%d nbatch %d: %s (fused %.1f us, two kernels %.1f us); ",
+           c ? " complex" : "", n, n, nb, best ? "fused kernel" : "two line kernels", t[1], t[0]);
   rep += buf;
   return GPE_OK;
 }
@@ -136,6 +198,8 @@ extern "C" gpe_status gpe_plan_autotune(gpe_plan plan, int levels) {
   if (levels < 1 || levels > 8) return fail(GPE_EINVAL, "levels must be in [1, 8]");
   std::string rep;
   gpe_status s = tune_lines(plan, rep);
+  if (s != GPE_OK) return s;
+  s = tune_fused(plan, rep);
   if (s != GPE_OK) return s;
   const GridHost& g = plan->g;
   if (g.disc == GPE_FOURIER && g.dim == 2 && g.v_kind != GPE_V_ARRAY) {

@@ -45,6 +45,13 @@ GridHost grid_coarsen(const GridHost& g, int levels_down);
 // engine's per-CTA share for single solves (4 KiB without an entry).
 int tuned_waves(int axis, int prec64, int cplx, int n0, int n1, int nbatch);
 void set_tuned_waves(int prec64, int cplx, int n0, int n1, int nbatch, int wx, int wy);
+// Fused 2D operator kernel or two line kernels for a float32 square grid n x n
+// (default without a measurement: fused for n <= 256).
+bool tuned_fused(int cplx, int n, int nbatch);
+void set_tuned_fused(int cplx, int n, int nbatch, int on);
+// gpe_set_operator_path: 0 automatic (measured or default choice), 1 the fused
+// kernel wherever it applies, 2 the two line kernels.
+int operator_path();
 int tuned_share_kb(int n0, int n1, int cplx);
 void set_tuned_share_kb(int n0, int n1, int cplx, int kb);
 // Time the cluster engine's float32 Algorithm 1 on grid g for each distinct
@@ -66,6 +73,13 @@ struct GridDev {
   FDGeom fd;
   int fd_blocks = 0;
   int max_blocks = 0;
+  // 2D Fourier grids (fused warp-line kernel, fused2d.cuh): per axis the
+  // twiddles e^{-2 pi i j k2 / F} in k2-major order (entry k2 * TPL + j, TPL
+  // the threads per line), and the launch's counters: task counter, exited
+  // warps, per-instance finished y- and x-tasks, error flag (zero between
+  // launches; the last warp of a launch resets them)
+  C* tw2[2] = {nullptr, nullptr};
+  unsigned int* fsync = nullptr;
   gpe_status create(const GridHost& g);
   void destroy();
 };
@@ -132,6 +146,11 @@ bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs, int* lch, int* P
                    unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share = 16 * 1024);
 
 void destroy_solver_cache(void* cache);
+
+// Polls after which a bounded device wait gives up (gpe_set_wait_limit;
+// 2^22 by default for grid barriers, 2^24 for the fused kernel's task waits,
+// whose polls are shorter).
+long long wait_limit(long long default_polls);
 
 // Instrumentation: launch counting and optional per-kernel CUDA-event timing.
 void instr_count(long long n);

@@ -192,6 +192,7 @@ struct PersistArgs {
   void* acc;            // kinetic accumulator
   unsigned int* bar;    // grid barrier: [0] arrivals, [1] generation
   int* err;             // set when a barrier wait gave up
+  long long max_polls;  // polls of one barrier wait before it gives up
   int max_loops;        // bound on the iterations (accepted + rejected trials)
   size_t tw_bytes;      // twiddle tables of all axes at the front of shared memory (16-byte multiple)
   unsigned long long* dbg;   // optional phase timestamps (globaltimer, CTA 0): [loop][4]

@@ -27,6 +27,7 @@
 #pragma once
 #include <stdlib.h>
 #include "ops_launch.cuh"
+#include "fused2d.cuh"
 
 namespace gpe {
 
@@ -581,10 +582,34 @@ template <typename T>
 gpe_status launch_lines2d(const GridHost& g, const GridDev<T>& d, const PassData<T>& D, int epi, void* acc,
                           bool step_first, cudaStream_t st, bool* handled) {
   *handled = false;
+  gpe_status s;
+  if constexpr (std::is_same<T, float>::value) {
+    const int path = operator_path();
+    const bool fused = path == 1 || (path == 0 && tuned_fused(g.is_complex, g.ext[0], g.nbatch));
+    if (fused2d_ok<T>(g) && fused && fused2d_enabled() && lines2d_enabled()) {
+#define GPE_F2D_CASE(E)                                                                    \
+  case E:                                                                                  \
+    s = g.is_complex ? fused2d_dispatch<T, true, E>(g, d, D, acc, step_first, st)           \
+                     : fused2d_dispatch<T, false, E>(g, d, D, acc, step_first, st);         \
+    break;
+      switch (epi) {
+        GPE_F2D_CASE(EPI_GRAD)
+        GPE_F2D_CASE(EPI_HESS)
+        GPE_F2D_CASE(EPI_F)
+        GPE_F2D_CASE(EPI_W)
+        GPE_F2D_CASE(EPI_RATIO)
+        GPE_F2D_CASE(EPI_WS)
+        default:
+          return GPE_OK;
+      }
+#undef GPE_F2D_CASE
+      if (s == GPE_OK) *handled = true;
+      return s;
+    }
+  }
   if (!lines2d_ok<T>(g) || !lines2d_enabled()) return GPE_OK;
   const int lf0 = ilog2(g.ext[0]), lf1 = ilog2(g.ext[1]);
   const int nb = g.nbatch;
-  gpe_status s;
 #define GPE_L2D_CASE(E)                                                                           \
   case E:                                                                                         \
     s = g.is_complex ? lines2d_dispatch0<T, true, E>(d, D, nb, acc, step_first, lf0, lf1, st)     \

@@ -525,10 +525,10 @@ static __device__ bool reduce_partials(A (&acc)[NQ], M amax2, int nq, double* pa
 }
 
 // Grid-wide barrier for a cooperative (co-resident) launch: arrival counter
-// bar[0] and generation bar[1].  Every wait is bounded: after ~2^22 polls
-// (about a second) the CTA sets *err and returns false, and so does every CTA
-// that later sees *err set.
-static __device__ bool grid_barrier(unsigned int* bar, int* err) {
+// bar[0] and generation bar[1].  Every wait is bounded: after max_polls polls
+// (2^22 by default, about a second) the CTA sets *err and returns false, and
+// so does every CTA that later sees *err set.
+static __device__ bool grid_barrier(unsigned int* bar, int* err, long long max_polls) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -545,7 +545,7 @@ static __device__ bool grid_barrier(unsigned int* bar, int* err) {
       long long polls = 0;
       while (*vgen == gen) {
         if (*verr) { ok = 0; break; }
-        if (++polls > (1LL << 22)) {
+        if (++polls > max_polls) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -714,8 +714,9 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
     c->best_res = resn;
     c->k_best = c->k;
   } else if (c->stall_iters > 0 && c->k - c->k_best >= c->stall_iters) {
+    // the precision floor: stopped, not converged (GPE_ENOCONV)
     c->done = 1;
-    c->status = 0;
+    c->status = 5;
   }
   if (!c->done && c->k >= c->max_iter) { c->done = 1; c->status = 5; }
   set_coef<R>(c);
@@ -758,12 +759,16 @@ static __device__ void rn_control(RNCtl* c, const double* r) {
 // ----------------------------------------------------------------- coherent loads
 // Inside a persistent launch, data written by other CTAs during the same launch
 // must bypass the (non-coherent) L1: ld.global.cg.
-template <bool COH, typename X> __device__ __forceinline__ X ldv(const X* p) {
-  if constexpr (COH) return __ldcg(p);
+// COH = 2: data that no thread writes during the launch, loaded through the
+// read-only path (the compiler may then issue the loads ahead of earlier
+// stores, which it must not do for plain loads of possibly aliasing arrays).
+template <int COH, typename X> __device__ __forceinline__ X ldv(const X* p) {
+  if constexpr (COH == 1) return __ldcg(p);
+  else if constexpr (COH == 2) return __ldg(p);
   else return *p;
 }
-template <bool COH, typename X> __device__ __forceinline__ X rdc(const X& r) {
-  if constexpr (COH) return *(const volatile X*)&r;
+template <int COH, typename X> __device__ __forceinline__ X rdc(const X& r) {
+  if constexpr (COH == 1) return *(const volatile X*)&r;
   else return r;
 }
 
@@ -779,7 +784,7 @@ struct EpiCtx {
   T nl, shift, lin_scale, th_c, delta, thk;
 };
 
-template <typename T, bool CPLX, int EPI, bool COH = false, typename A>
+template <typename T, bool CPLX, int EPI, int COH = 0, typename A>
 __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long long gi,
                                                typename VT<T, CPLX>::V x,
                                                typename VT<T, CPLX>::V lin, A (&acc)[NQ], T& amax) {
@@ -887,7 +892,7 @@ __device__ __forceinline__ void epilogue_point(const EpiCtx<T, CPLX>& E, long lo
   }
 }
 
-template <typename T, bool CPLX, int EPI, bool COH = false>
+template <typename T, bool CPLX, int EPI, int COH = 0>
 __device__ __forceinline__ void make_ctx(EpiCtx<T, CPLX>& E, const PassData<T>& D) {
   using V = typename VT<T, CPLX>::V;
   E.out = (V*)D.out;
@@ -1197,7 +1202,7 @@ __global__ void __launch_bounds__(NTHREADS) k_alg1_persist(PersistArgs<T> P) {
           block_partial(acc, amax, NQ, P.D.partials + (size_t)blk * NQ);
         }
       }
-      if (!grid_barrier(P.bar, P.err)) {
+      if (!grid_barrier(P.bar, P.err, P.max_polls)) {
         writeback();
         return;
       }

@@ -25,6 +25,10 @@ static inline int ilog2(int v) {
 
 constexpr int TARGET_CTAS = 2 * 152;
 
+// Threads per line of the fused warp-line FFT (fused2d.cuh) for a line of F
+// points: F = TPL x PPT with PPT >= TPL points per thread.
+static inline int fused_tpl(int F) { return F <= 128 ? 8 : (F <= 512 ? 16 : 32); }
+
 // Tile shape of a line pass along `axis` of an array with extents ext, lines of
 // FFT length Fbuf in shared memory (Fbuf >= F when the lines grow, prolongation).
 template <typename T>
@@ -131,6 +135,30 @@ gpe_status GridDev<T>::create(const GridHost& g) {
       }
       geom[a] = G;
       max_blocks = std::max(max_blocks, blocks[a]);
+      if (g.dim == 2 && F >= 64 && F <= 1024) {
+        // k2-major twiddles of the fused kernel's line FFT (F = TPL x PPT)
+        const int tpl = fused_tpl(F), ppt = F / tpl;
+        std::vector<Cx> h2(F);
+        for (int k2 = 0; k2 < ppt; ++k2)
+          for (int j = 0; j < tpl; ++j) {
+            const double ang = -2.0 * M_PI * (double)((j * k2) % F) / (double)F;
+            h2[k2 * tpl + j].x = (T)cos(ang);
+            h2[k2 * tpl + j].y = (T)sin(ang);
+          }
+        GPE_CUDA(cudaMalloc(&tw2[a], sizeof(Cx) * F));
+        GPE_CUDA(cudaMemcpy(tw2[a], h2.data(), sizeof(Cx) * F, cudaMemcpyHostToDevice));
+      }
+    }
+    if (g.dim == 2) {
+      // per-task partial sums of the fused kernel: one slot per x-task
+      if (g.disc == GPE_FOURIER && g.ext[0] >= 64 && g.ext[0] <= 1024) {
+        const int lines = g.is_complex ? g.ext[1] : g.ext[1] / 2;
+        const int lpw = 32 / fused_tpl(g.ext[0]);
+        max_blocks = std::max(max_blocks, std::max(1, lines / lpw) * g.nbatch);
+      }
+      const size_t nsync = 3 + 2 * (size_t)g.nbatch;
+      GPE_CUDA(cudaMalloc(&fsync, sizeof(unsigned int) * nsync));
+      GPE_CUDA(cudaMemset(fsync, 0, sizeof(unsigned int) * nsync));
     }
   } else {
     fd.dim = g.dim;
@@ -163,6 +191,12 @@ void GridDev<T>::destroy() {
     lam[a] = nullptr;
     coord[a] = nullptr;
   }
+  for (int a = 0; a < 2; ++a) {
+    cudaFree(tw2[a]);
+    tw2[a] = nullptr;
+  }
+  cudaFree(fsync);
+  fsync = nullptr;
 }
 
 // Opt in to `bytes` of dynamic shared memory (static shared memory counts
@@ -431,6 +465,7 @@ gpe_status launch_alg1_persist(const GridHost& g, const GridDev<T>& d, const Pas
   P.bar = bar;
   P.err = err;
   P.max_loops = max_loops;
+  P.max_polls = wait_limit(1LL << 22);
   size_t twb = 0;
   for (int a = 0; a < g.dim; ++a) twb += (size_t)d.geom[a].F * sizeof(typename C2t<T>::type);
   P.tw_bytes = (twb + 15) & ~(size_t)15;

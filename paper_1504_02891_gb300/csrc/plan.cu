@@ -303,6 +303,17 @@ static gpe_status read_energy(gpe_plan p, double* E, double* mu, double* norm2) 
   GPE_CUDA(cudaMemcpyAsync(p->sc.h_results, p->sc.results, sizeof(double) * NQ * nb, cudaMemcpyDeviceToHost, p->stream));
   GPE_CUDA(cudaStreamSynchronize(p->stream));
   gpe_status st = GPE_OK;
+  // a bounded task wait of the fused 2D kernel that gave up leaves its flag set
+  // (and NaN partial sums): report it as the expired wait it was, then clear it
+  unsigned int* fs = p->prec == GPE_F32 ? p->d32->fsync : p->d64->fsync;
+  if (fs) {
+    unsigned int flag = 0;
+    GPE_CUDA(cudaMemcpy(&flag, fs + 2 + 2 * (size_t)nb, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) {
+      GPE_CUDA(cudaMemset(fs + 2 + 2 * (size_t)nb, 0, sizeof(flag)));
+      return fail(GPE_ETIMEOUT, "a bounded task wait of the fused 2D operator kernel expired");
+    }
+  }
   for (int b = 0; b < nb; ++b) {
     const double* r = p->sc.h_results + (size_t)b * NQ;
     const double e2 = r[0], e4 = r[1], n2 = r[2];
@@ -408,6 +419,31 @@ extern "C" gpe_status gpe_prolong(gpe_plan c, gpe_plan f, const void* psi_c, voi
 }
 
 extern "C" int64_t gpe_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+namespace gpe {
+static std::atomic<long long> g_wait_limit{0};
+long long wait_limit(long long default_polls) {
+  const long long v = g_wait_limit.load();
+  return v > 0 ? v : default_polls;
+}
+}  // namespace gpe
+
+namespace gpe {
+static std::atomic<int> g_op_path{0};
+int operator_path() { return g_op_path.load(); }
+}  // namespace gpe
+
+extern "C" gpe_status gpe_set_operator_path(int path) {
+  if (path < 0 || path > 2) return fail(GPE_EINVAL, "path must be 0, 1 or 2");
+  gpe::g_op_path.store(path);
+  return GPE_OK;
+}
+
+extern "C" gpe_status gpe_set_wait_limit(int64_t polls) {
+  if (polls < 0) return fail(GPE_EINVAL, "polls must be >= 0");
+  gpe::g_wait_limit.store((long long)polls);
+  return GPE_OK;
+}
 
 extern "C" gpe_status gpe_profile_enable(int on) {
   if (!on) prof_clear();
