@@ -45,10 +45,32 @@ L2_FLUSH_BYTES = 256 << 20
 # the trial point Y); the ratio pass (read Z, X^k, G^k).  Per real number: 4 B
 # (float32) or 8 B (float64); complex doubles it.
 ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5, "acc": 2}
-# DRAM bytes (read + write) of one H psi apply of the happly workload, from the
-# ncu capture summarised in profiles/happly_64x512sq_c64_lines.txt (k_lines_y
-# 227.6 MB + k_lines_x 373.9 MB); must be re-taken whenever those kernels change.
-HAPPLY_DRAM_BYTES_PER_APPLY = 601.2e6
+# DRAM bytes (read + write) of one H psi apply of the happly workload come
+# from an ncu capture recorded in profiles/happly_traffic.json together with a
+# SHA-256 of the kernel sources it was taken with; once any of those sources
+# changes the figure no longer describes the kernel and is reported as null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "happly_traffic.json")
+KERNEL_SOURCES = ["fused2d.cuh", "lines2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"]
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1504_02891_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """(bytes per apply, note) from the committed ncu record, or (None, why)."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None, "no ncu traffic record"
+    if rec.get("kernel_sources_sha256") != kernel_sources_sha256():
+        return None, "kernel sources changed since the ncu traffic capture"
+    return float(rec["dram_bytes_per_apply"]), rec.get("capture", "")
 
 
 def parse():
@@ -195,7 +217,7 @@ def roofline_from_profile(prof, peaks):
             continue
         kern, size = name.split("@")
         parts = kern.split("_")             # pass_f32_r_W
-        if parts[0] not in ("pass", "fd", "step", "linesy", "linesx"):
+        if parts[0] not in ("pass", "fd", "step", "linesy", "linesx", "fused2d"):
             continue
         key = (parts[1], parts[2], int(size))
         g = groups.setdefault(key, {"ms": 0.0, "final": {}, "kernels": {}})
@@ -284,25 +306,66 @@ def happly_throughput(G, torch, W, peaks, reps=20):
     plan.close()
     hess = {"bound": "hbm", "achieved": alg_h / (ms_h * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
             "frac": alg_h / (ms_h * 1e-3) / 1e9 / peak, "traffic": None,
-            "kernel": "Hessian-vector product (gpe_hessvec) = k_lines_y + k_lines_x, same batch",
+            "kernel": "",
             "us_per_apply": ms_h * 1e3, "alg_bytes_per_apply": alg_h}
+    traffic, tnote = measured_traffic()
+    fused = "512x512 nbatch 64: fused kernel" in G.autotune_report()
+    kern = ("k_fused2d (one persistent launch: warp-per-line FFTs, y- and x-tasks per instance)" if fused else
+            "k_lines_y + k_lines_x (two register-FFT line kernels)")
+    hess["kernel"] = f"Hessian-vector product (gpe_hessvec) = {kern}, same batch"
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "hessvec": hess,
-            "traffic": HAPPLY_DRAM_BYTES_PER_APPLY,
-            "kernel": "H psi apply = k_lines_y + k_lines_x (register-FFT line kernels), "
-                      "64 x 512^2 complex64 rotating (Omega=0.9), float32",
-            "us_per_apply": ms * 1e3, "alg_bytes_per_apply": alg, "launches_per_apply": 2,
+            "traffic": traffic, "traffic_source": tnote,
+            "kernel": f"H psi apply = {kern}, 64 x 512^2 complex64 rotating (Omega=0.9), float32, "
+                      "implementation chosen by gpe_plan_autotune",
+            "us_per_apply": ms * 1e3, "alg_bytes_per_apply": alg, "launches_per_apply": 1 if fused else 2,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+
+
+def config3_times(G, torch, W):
+    """Config 3 (3D sine 128^3, depth-100 lattice, beta = 1600, cascade
+    32^3 -> 64^3 -> 128^3): time to ||H psi - mu psi||_h <= 1e-9 (or Eq.
+    crit2), mixed schedule against plain float64, one warm-up and one timed
+    solve each (CUDA events on the caller's stream)."""
+    p = W.config("c3")
+    out = {"workload": "3D sine 128^3 (127^3 unknowns), V = |x|^2/2 + 100 sum sin^2(pi x/4), beta = 1600, "
+                       "Gaussian init, cascade 32^3->64^3->128^3"}
+    with G.Plan(p, prec=G.F64) as plan:
+        init = G.to_device(W.gaussian(p))
+        st = torch.cuda.current_stream()
+        for name, mode in (("mixed", 1), ("fp64", 0)):
+            work = init.clone()
+            plan.solve(work, mode=mode, levels=3, res_tol=RES_TOL)
+            work.copy_(init)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            r = plan.solve(work, mode=mode, levels=3, res_tol=RES_TOL)
+            e1.record(st)
+            torch.cuda.synchronize()
+            out[name] = {"time_s": e0.elapsed_time(e1) / 1e3, "E": r["E"], "res": r["res"],
+                         "outer_f64": r["outer_f64"]}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    out["delta_E_rel_mixed_vs_fp64"] = abs(out["mixed"]["E"] - out["fp64"]["E"]) / abs(out["fp64"]["E"])
+    return out
+
+
+SWEEP_FP64_SAMPLE = 16
 
 
 def sweep_throughput(G, torch, W, np):
     """Config 5, the batched sweep: 256 independent 2D rotating problems
     (grids 64^2-256^2, beta, Omega, gamma_y drawn from the seeded sweep), one
     gpe_solve_batch call (float32 Algorithm 1, float64 sums, each instance to
-    its float32 floor or 1e-7) against the same 256 solves one call each."""
+    ||H psi - mu psi||_h <= 1e-7 or its float32 floor), against (a) the same
+    256 problems one gpe_solve_batch call each and (b) plain float64
+    gpe_rnewton_solve calls one problem at a time (Algorithm 2, float64
+    throughout, the same tolerance), timed on the first SWEEP_FP64_SAMPLE
+    problems and scaled to 256."""
     ps = W.batched_sweep(256)
-    init = [torch.from_numpy(W.sweep_initial(p, i).astype(np.complex64)).cuda() for i, p in enumerate(ps)]
-    opts = dict(max_iter=1000, res_tol=1e-7)
+    init_np = [W.sweep_initial(p, i) for i, p in enumerate(ps)]
+    init = [torch.from_numpy(a.astype(np.complex64)).cuda() for a in init_np]
+    opts = dict(max_iter=1000, res_tol=1e-7, mode=2)
     G.solve_batch(ps[:8], [t.clone() for t in init[:8]], **opts)
     x = [t.clone() for t in init]
     torch.cuda.synchronize()
@@ -310,6 +373,13 @@ def sweep_throughput(G, torch, W, np):
     reps = G.solve_batch(ps, x, **opts)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
+    # the mixed schedule batched: float32 stage + float64 refinement (<= 30 outer steps each)
+    x = [t.clone() for t in init]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps_m = G.solve_batch(ps, x, max_iter=1000, res_tol=1e-7, mode=1, max_outer=30)
+    torch.cuda.synchronize()
+    tm = time.perf_counter() - t0
     x = [t.clone() for t in init]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -317,12 +387,32 @@ def sweep_throughput(G, torch, W, np):
         G.solve_batch([p], [x[i]], **opts)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
+    # plain float64 solves, one problem per call (plan creation untimed)
+    t64, conv64 = 0.0, 0
+    for i in range(SWEEP_FP64_SAMPLE):
+        with G.Plan(ps[i], prec=G.F64) as plan:
+            t = G.to_device(init_np[i], G.F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = plan.solve(t, mode=0, levels=1, res_tol=1e-7, max_outer=200)
+            torch.cuda.synchronize()
+            t64 += time.perf_counter() - t0
+            conv64 += int(r["status"] == 0 and r["res"] <= 1e-7)
     its = [r["inner_f32"] for r in reps]
     return {"workload": "256 x 2D rotating (64^2/128^2/256^2 on [-12,12]^2, beta~U[100,1000], "
                         "Omega~U[0,0.9], gamma_y~U[1,1.2]), complex64 bulk, float64 sums",
             "batched_solves_per_s": 256 / tb, "sequential_solves_per_s": 256 / ts, "speedup": ts / tb,
+            "sequential_fp64_solves_per_s": SWEEP_FP64_SAMPLE / t64,
+            "speedup_vs_sequential_fp64": (t64 / SWEEP_FP64_SAMPLE * 256) / tb,
+            "fp64_sample": f"first {SWEEP_FP64_SAMPLE} problems, plain float64 gpe_rnewton_solve each, "
+                           f"scaled to 256; {conv64} of {SWEEP_FP64_SAMPLE} reached res 1e-7 within 200 outer steps",
             "batched_ms": tb * 1e3, "iterations_median": float(np.median(its)), "iterations_max": int(max(its)),
-            "converged": int(sum(1 for r in reps if r["status"] == 0))}
+            "converged": int(sum(1 for r in reps if r["status"] == 0 and r["res"] <= 1e-7)),
+            "stopped_at_float32_floor": int(sum(1 for r in reps if r["status"] == 5)),
+            "mixed_batched": {"solves_per_s": 256 / tm, "ms": tm * 1e3,
+                              "converged_res_1e-7": int(sum(1 for r in reps_m if r["status"] == 0)),
+                              "outer_f64_median": float(np.median([r["outer_f64"] for r in reps_m])),
+                              "speedup_vs_sequential_fp64": (t64 / SWEEP_FP64_SAMPLE * 256) / tm}}
 
 
 def our_arm(args):
@@ -417,6 +507,7 @@ def our_arm(args):
     prof = G.profile_summary()
     G.profile_enable(False)
     roof = roofline_from_profile(prof, peaks)
+    c3 = config3_times(G, torch, W)
     happly = happly_throughput(G, torch, W, peaks)
     sweep = sweep_throughput(G, torch, W, np)
 
@@ -427,7 +518,7 @@ def our_arm(args):
         return
 
     cpu = None
-    dE = None
+    dE = dE64 = None
     if not args.no_cpu_baseline:
         try:
             r = run_oracle(args.cpu_seconds, 50, threads=1)
@@ -436,19 +527,24 @@ def our_arm(args):
                    "sample": f"{len(r['times'])} complete FP64 oracle cascade solves of the same workload "
                              "(numpy, dense DFT matrices, BLAS pinned to 1 thread)"}
             dE = abs(reps_mixed[-1]["E"] - r["E"]) / abs(r["E"])
+            dE64 = abs(reps_fp64[-1]["E"] - r["E"]) / abs(r["E"])
         except Exception as e:  # reported, never fatal
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
     rep = reps_mixed[-1]
     line = {
-        "metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": ms_mixed / 1e3, "unit": "s",
+        "fp64_time_s": ms_fp64 / 1e3, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
+        "delta_E_rel_vs_oracle": dE, "delta_E_rel_vs_oracle_fp64": dE64,
+        "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [256, 256], "levels": 3, "beta": 1000.0,
                    "l2": "flushed between steps (256 MiB write, untimed); each step timed with CUDA events",
                    "parallelism": f"replicas x{world} (no data-path collective)"},
-        "fp64_time_s": ms_fp64 / 1e3, "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed,
         "throughput": {"value": world * 1e3 / ms_mixed, "unit": "ground states/s"},
-        "E": rep["E"], "mu": rep["mu"], "res": rep["res"], "delta_E_rel_vs_oracle": dE,
+        "E": rep["E"], "mu": rep["mu"], "res": rep["res"],
+        "E_fp64": reps_fp64[-1]["E"], "res_fp64": reps_fp64[-1]["res"],
+        "c3": c3,
         "solver": {k: rep[k] for k in ("outer_f32", "outer_f64", "inner_f32", "inner_f64", "nfe", "ms_f32", "ms_f64")},
         "roofline": happly, "solve_operator_roofline": roof,
         "autotune": G.autotune_report() + ("".join(f" failed: {e};" for e in AUTOTUNE_ERRORS)),

@@ -216,10 +216,16 @@ gpe_status gpe_rnewton_solve(gpe_plan plan, void* psi_inout, const gpe_solve_opt
 gpe_status gpe_hess_min_eig(gpe_plan plan, const void* psi, int max_iter, double tol, double* lambda_min,
                             double* residual, int* iters);
 
-/* Many independent ground-state problems in one call: Algorithm 1 (Theorem
- * 3.3 step, Eq. bb-1 BB step, Eq. NMLS-Armijo search) in float32 with float64
- * reductions and device-side control for every instance at once -- the
- * float32 bulk of the mixed schedule, batched.  problems[i] (i < n): 2D
+/* Many independent ground-state problems in one call: the mixed schedule,
+ * batched.  First Algorithm 1 (Theorem 3.3 step, Eq. bb-1 BB step, Eq.
+ * NMLS-Armijo search) in float32 with float64 reductions and device-side
+ * control for every instance at once; then (opts->mode 1, the default) for
+ * every instance that has not reached res_tol, the float64 refinement of the
+ * mixed schedule: Algorithm 2 (Eq. TR-ratio, update-X, tau-up) with float64
+ * outer quantities and float32 difference-form subproblems, at most
+ * max_outer outer steps (k_sub, delta0 as in gpe_rnewton_solve; Eq. crit2 is
+ * not used: an instance stops at res_tol or max_outer).  mode 2: the float32
+ * stage only.  Other modes: GPE_EINVAL.  problems[i] (i < n): 2D
  * Fourier grids whose state fits one thread-block cluster (n[0], n[1] powers
  * of two, up to 256^2; real with omega = 0, or complex); each instance has
  * its own beta, omega and potential.  Instances with the same grid (extents,
@@ -231,9 +237,15 @@ gpe_status gpe_hess_min_eig(gpe_plan plan, const void* psi, int max_iter, double
  * max_iter bounds the iterations per instance; an instance stops when
  * ||H psi - mu psi||_h <= res_tol, or ||A(X)X|| <= switch_rel |X^*G|, or after
  * 40 accepted steps without a new smallest residual (the float32 floor).
- * reports[i] receives E, mu and res of the final evaluation (float64 sums of
- * float32 values), inner_f32 (iterations), nfe, and status GPE_OK, GPE_ENOCONV
- * (max_iter reached) or GPE_ENONFINITE.  Runs on cuda_stream (NULL = legacy
+ * The states are returned in float32 (after a refinement: the float64 state
+ * rounded to float32).  reports[i] receives E, mu and res of the final
+ * evaluation (float32 stage: float64 sums of float32 values; refined: the
+ * float64 state), inner_f32 / outer_f64 / inner_f64 (iterations), nfe,
+ * ms_f32 (the float32 stage's time per instance of its group), ms_f64 (the
+ * refinement of that instance), and status GPE_OK when res <= res_tol,
+ * GPE_ENOCONV when an instance stopped short of it (max_iter, the float32
+ * floor or switch_rel in mode 2, max_outer after a refinement), or
+ * GPE_ENONFINITE.  Runs on cuda_stream (NULL = legacy
  * default stream) and synchronises; allocates its own scratch per call.
  * Returns GPE_EINVAL for a grid outside the above and GPE_ENONFINITE if any
  * instance went non-finite (the other states are still written). */
@@ -250,8 +262,9 @@ gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* const* psi,
  *     gives a distinct cluster size;
  * and records the fastest choices in a process-wide table keyed by grid (and
  * batch), which every later launch on those shapes uses (without an entry:
- * 4 waves, 4 KiB).  Computed values do not change (reductions may differ by
- * rounding order).  Other grids: nothing to tune, GPE_OK.  Allocates scratch
+ * 4 waves, 4 KiB).  Launch shapes do not change computed values (reductions
+ * may differ by rounding order); the fused-or-two-kernel choice changes the
+ * FFT factorisation, so operator values agree to rounding.  Other grids: nothing to tune, GPE_OK.  Allocates scratch
  * of two plan vectors and one solver level per grid; synchronises.  Not
  * thread-safe with concurrent launches on the tuned shapes.
  *   - float32 square grids: the fused one-launch operator kernel against the
@@ -306,7 +319,8 @@ int64_t gpe_kernel_launches(void);
  * no counterpart: an implementation choice that never changes the operator's
  * values beyond rounding order).  path 0: automatic -- the choice
  * gpe_plan_autotune measured for the grid and batch, else the fused kernel
- * for lines of up to 256 points; 1: always the fused one-launch kernel;
+ * for batches of at least 16 real fields on grids up to 256^2; 1: always the
+ * fused one-launch kernel;
  * 2: always the two line kernels.  Process-wide, for later launches; a
  * diagnostic and test knob.  Errors: GPE_EINVAL (path outside 0..2). */
 gpe_status gpe_set_operator_path(int path);

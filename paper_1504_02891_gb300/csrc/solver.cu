@@ -199,6 +199,7 @@ struct RunStats {
 
 struct SolveParams {
   int k_init, k_sub, max_outer, max_iter, method, chunk, use_graphs, persistent, cluster, search;
+  int refine = 0;      // gpe_solve_batch: float64 refinement after the float32 bulk
   double eps0, delta_stop, res_tol_X, delta0, switch_rel, alpha_hat, eta;
 };
 
@@ -527,6 +528,8 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
       if (rejects >= 4) break;
     }
   }
+  // the last allowed outer step may itself have reached the tolerance
+  if (res_tol > 0.0 && resk <= res_tol) ls.converged = true;
   ls.F = Fk;
   ls.res = resk;
   ls.theta = thk;
@@ -1169,6 +1172,39 @@ struct BatchGroup {
   }
 };
 
+// Point a level built for one problem of a group at another problem on the
+// same grid (extents, box, complexity): its potential, beta and Omega.  The
+// level's cached CUDA graphs captured the old operator and are dropped.
+template <typename T>
+static gpe_status level_set_problem(Level<T>& L, const GridHost& gi) {
+  L.g.beta = gi.beta;
+  L.g.omega = gi.omega;
+  std::vector<T> hv((size_t)L.M);
+  for (long long i = 0; i < L.M; ++i) hv[(size_t)i] = (T)gi.V[(size_t)i];
+  GPE_CUDA(cudaMemcpy(L.d.V, hv.data(), sizeof(T) * hv.size(), cudaMemcpyHostToDevice));
+  if (L.g.disc != GPE_FD) {
+    for (int a = 0; a < 2 && a < L.g.dim; ++a) {
+      PassGeom<T>& G = L.d.geom[a];
+      if (gi.omega != 0.0) {
+        G.c1 = (T)((a == 0 ? gi.omega : -gi.omega) / G.F);
+        G.rcoord = L.d.coord[a == 0 ? 1 : 0];
+      } else {
+        G.c1 = (T)0;
+        G.rcoord = nullptr;
+      }
+    }
+  }
+  L.d.fd.omega = gi.omega;
+  const float om = (float)gi.omega;
+  GPE_CUDA(cudaMemcpy(L.d_omega, &om, sizeof(float), cudaMemcpyHostToDevice));
+  for (int i = 0; i < 3; ++i)
+    if (L.chunk_exec[i]) {
+      cudaGraphExecDestroy(L.chunk_exec[i]);
+      L.chunk_exec[i] = nullptr;
+    }
+  return GPE_OK;
+}
+
 static bool same_grid(const GridHost& a, const GridHost& b) {
   return a.ext[0] == b.ext[0] && a.ext[1] == b.ext[1] && a.is_complex == b.is_complex && a.lo[0] == b.lo[0] &&
          a.lo[1] == b.lo[1] && a.hi[0] == b.hi[0] && a.hi[1] == b.hi[1];
@@ -1238,6 +1274,7 @@ static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh
   A.ctl = B.ctl;
   A.results = B.sc.results;
   A.next = B.next;
+  auto t0 = std::chrono::steady_clock::now();
   s = launch_cluster_alg1(A, cplx, st);
   if (s != GPE_OK) return s;
   // results back to psi (physical units) and the reports
@@ -1248,6 +1285,7 @@ static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh
   }
   GPE_CUDA(cudaMemcpyAsync(hc.data(), B.ctl, sizeof(Alg1Ctl) * n, cudaMemcpyDeviceToHost, st));
   GPE_CUDA(cudaStreamSynchronize(st));
+  const double ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / n;
   for (int k = 0; k < n; ++k) {
     const Alg1Ctl& c = hc[k];
     gpe_solve_report& r = reports[B.idx[k]];
@@ -1255,9 +1293,58 @@ static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh
     r.E = c.F_cur;
     r.mu = 0.5 * c.theta_c;
     r.res = 0.5 * c.res;
-    r.status = c.status == 4 ? GPE_ENONFINITE : (c.status == 5 ? GPE_ENOCONV : GPE_OK);
+    // an instance that met res_tol converged; one that stopped at switch_rel
+    // or at the float32 floor did not reach the stated tolerance
+    r.status = c.status == 4 ? GPE_ENONFINITE : ((c.status == 5 || r.res > 0.5 * P.res_tol_X) ? GPE_ENOCONV : GPE_OK);
     r.inner_f32 = c.k;
     r.nfe = c.nfe;
+    r.ms_f32 = ms32;
+  }
+  if (!P.refine) return GPE_OK;
+  // float64 refinement (the mixed schedule's finest level, per instance):
+  // Algorithm 2 with float64 outer quantities and float32 difference-form
+  // subproblems in the cluster engine, from the float32 state, for every
+  // instance that did not reach res_tol
+  struct LevelPair {
+    Level<double> d;
+    Level<float> f;
+    ~LevelPair() {
+      d.destroy();
+      f.destroy();
+    }
+  };
+  std::unique_ptr<LevelPair> LP(new LevelPair());
+  Level<double>* Ld = &LP->d;
+  Level<float>* Lf = &LP->f;
+  s = Ld->create(g);
+  if (s == GPE_OK) s = Lf->create(g);
+  if (s != GPE_OK) return s;
+  for (int k = 0; k < n; ++k) {
+    gpe_solve_report& r = reports[B.idx[k]];
+    if (r.status == GPE_ENONFINITE || r.status == GPE_OK) continue;
+    const GridHost& gi = gh[B.idx[k]];
+    auto t1 = std::chrono::steady_clock::now();
+    s = level_set_problem<double>(*Ld, gi);
+    if (s == GPE_OK) s = level_set_problem<float>(*Lf, gi);
+    if (s != GPE_OK) return s;
+    s = launch_convert<float, double>((const float*)((char*)B.x + vbytes * k), (double*)Ld->xs[0], nreal, 1.0, st);
+    if (s == GPE_OK) s = normalise_slot0<double>(*Ld, st);
+    if (s != GPE_OK) return s;
+    LevelStats l2;
+    s = rn_run<double>(*Ld, P, 0, false, st, l2, 2.0 * r.mu, Lf);
+    if (s != GPE_OK) return s;
+    s = launch_convert<double, float>((const double*)Ld->xk, (float*)psi[B.idx[k]], nreal, 1.0 / sh, st);
+    if (s != GPE_OK) return s;
+    GPE_CUDA(cudaStreamSynchronize(st));
+    r.E = l2.F;
+    r.mu = 0.5 * l2.theta;
+    r.res = 0.5 * l2.res;
+    r.status = l2.converged ? GPE_OK : GPE_ENOCONV;
+    r.outer_f64 = l2.outer;
+    r.inner_f64 = l2.inner;
+    r.inner_f32 += l2.inner32;
+    r.nfe += l2.nfe;
+    r.ms_f64 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
   }
   return GPE_OK;
 }
@@ -1284,6 +1371,7 @@ extern "C" gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* 
         !cluster_shape(g.ext[0], g.ext[1], g.is_complex, 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp))
       return fail(GPE_EINVAL, "gpe_solve_batch takes 2D Fourier grids whose state fits one cluster (<= 256^2)");
   }
+  if (o.mode != 1 && o.mode != 2) return fail(GPE_EINVAL, "gpe_solve_batch: mode must be 1 (mixed) or 2 (float32)");
   SolveParams P{};
   P.max_iter = o.max_iter;
   P.search = o.search;
@@ -1292,6 +1380,17 @@ extern "C" gpe_status gpe_solve_batch(const gpe_problem* problems, int n, void* 
   P.eps0 = o.eps0;
   P.res_tol_X = 2.0 * o.res_tol;
   P.switch_rel = o.switch_rel;
+  // the float64 refinement (mode 1) runs Algorithm 2 with these
+  P.refine = o.mode == 1 && o.res_tol > 0.0;
+  P.k_init = 0;
+  P.k_sub = o.k_sub;
+  P.max_outer = o.max_outer;
+  P.chunk = o.chunk;
+  P.use_graphs = o.use_graphs;
+  P.persistent = o.persistent;
+  P.cluster = o.cluster;
+  P.delta_stop = 0.0;        // stop on res_tol (or max_outer), not on Eq. crit2
+  P.delta0 = o.delta0;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // group the instances by grid; one cluster launch per group
   std::vector<std::unique_ptr<BatchGroup>> groups;

@@ -1,5 +1,8 @@
 """gpe_plan_autotune: measured launch shapes for the line kernels and the
-cluster engine change how the work is spread, not what is computed."""
+cluster engine change how the work is spread, not what is computed; the
+measured choice between the fused operator kernel and the two line kernels
+changes the FFT factorisation, so the operator values agree to float32
+rounding (identical bytes when the implementation stays the same)."""
 import numpy as np
 import pytest
 
@@ -24,9 +27,10 @@ def test_autotune_keeps_operator_values_and_records_choices():
         plan.autotune(levels=3)
         plan.grad(psi, out1)
         torch.cuda.synchronize()
-        assert torch.equal(out0, out1)
-    rep = G.autotune_report()
+        rep = G.autotune_report()
+        assert float((out0 - out1).abs().max()) <= 2e-5 * float(out0.abs().max())
     assert "lines f32 256x256 nbatch 4" in rep, rep
+    assert "operator f32 256x256 nbatch 4:" in rep, rep
     for n in (256, 128, 64):
         assert f"cluster {n}x{n}: share" in rep, rep
 
