@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--only", choices=["happly", "solve"], default=None,
                     help="profiling aid: run only the H-apply loop (3 warm-up + 10 applies) or only two "
                          "mixed solves of the workload, print a one-line summary, no JSON contract line")
+    ap.add_argument("--happly-path", type=int, choices=[0, 1, 2], default=0,
+                    help="with --only happly: 0 = autotuned implementation, 1 = the fused kernel, 2 = the two "
+                         "line kernels (1 and 2 skip the autotuning, so the launch sequence is fixed)")
     return ap.parse_args()
 
 
@@ -571,7 +574,10 @@ def profiling_run(args):
     if args.only == "happly":
         p = W.config("c4")
         plan = G.Plan(p, nbatch=64, prec=G.F32)
-        plan.autotune()
+        if args.happly_path == 0:
+            plan.autotune()
+        else:
+            G.set_operator_path(args.happly_path)
         psi = plan.empty()
         psi.real.normal_()
         psi.imag.normal_()

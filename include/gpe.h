@@ -319,7 +319,7 @@ int64_t gpe_kernel_launches(void);
  * no counterpart: an implementation choice that never changes the operator's
  * values beyond rounding order).  path 0: automatic -- the choice
  * gpe_plan_autotune measured for the grid and batch, else the fused kernel
- * for batches of at least 16 real fields on grids up to 256^2; 1: always the
+ * for batches of at least 16 instances on grids up to 256^2; 1: always the
  * fused one-launch kernel;
  * 2: always the two line kernels.  Process-wide, for later launches; a
  * diagnostic and test knob.  Errors: GPE_EINVAL (path outside 0..2). */

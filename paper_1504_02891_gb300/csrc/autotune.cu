@@ -14,7 +14,7 @@
 //     (fused2d.cuh) or the two line kernels, whichever applies the operator
 //     faster for the grid and batch.
 // Launches with no table entry use the fixed rule (4 waves; 4 KiB; the fused
-// kernel for batches of >= 16 real fields on grids up to 256^2).  The
+// kernel for batches of >= 16 instances on grids up to 256^2).  The
 // choice never changes what is computed, only how the work is spread: the
 // operator values are identical, reductions may differ by rounding order.
 #include <map>
@@ -36,10 +36,10 @@ std::map<std::tuple<int, int, int>, int> g_fused;                            // 
 bool tuned_fused(int cplx, int n, int nbatch) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_fused.find(std::make_tuple(cplx, n, nbatch));
-  // without a measurement: the fused kernel for batches of real fields on
-  // grids up to 256^2 (faster there on GB300; a single instance waits for its
-  // own y-tasks and is faster with the two line kernels)
-  if (it == g_fused.end()) return !cplx && n <= 256 && nbatch >= 16;
+  // without a measurement: the fused kernel for batches on grids up to 256^2
+  // (faster there on GB300; a single instance waits for its own y-tasks and
+  // is faster with the two line kernels, and so are 512^2 and 1024^2 lines)
+  if (it == g_fused.end()) return n <= 256 && nbatch >= 16;
   return it->second != 0;
 }
 

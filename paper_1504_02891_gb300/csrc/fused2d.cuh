@@ -286,14 +286,20 @@ __global__ void __launch_bounds__(FUSED_THREADS, fused_minb(LF)) k_fused2d(PassG
     if (t >= ntask) break;
     int kind, b, ti;
     decode_task(t, nb, NY, NX, FA.skew, kind, b, ti);
+    // Both kinds of task share one copy of the line transform below: four
+    // unrolled copies of it (y and x, forward and inverse) overflow the
+    // instruction cache.  Every load of a task is issued before its first
+    // store (a store in between would hold the later loads back); read-only
+    // operands go through the non-coherent path.
+    C v[PPT];
+    int ok = 1;
+    long long cb = 0, rb = 0, ib = 0;
+    int row0 = 0;
+    FusedSym<T, F> sym;
     if (kind == 0) {
       // ---------------- y-task: columns ti*LPW + h (complex view)
       const int ccol = ti * LPW + h;
-      const long long cb = (long long)b * (CPLX ? M : M >> 1) + ccol;
-      // every load of a task is issued before its first store (a store in
-      // between would hold the later loads back); the operands are read-only
-      // during the launch
-      C v[PPT];
+      cb = (long long)b * (CPLX ? M : M >> 1) + ccol;
       if (yst) {
 #pragma unroll
         for (int s = 0; s < PPT; ++s) {
@@ -313,18 +319,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, fused_minb(LF)) k_fused2d(PassG
           v[s] = a;
         }
       }
-      FusedSym<T, F> sym;
       sym.c2 = gy.c2;
       sym.dl = gy.dlam;
       sym.c1c = (CPLX && gy.rcoord) ? gy.c1 * gy.rcoord[ccol] : T(0);
-      FFT::apply(v, ex, twy, j, sym);
-#pragma unroll
-      for (int s = 0; s < PPT; ++s) tyc[cb + (long long)(j + TPL * s) * n0c] = v[s];
-      __syncwarp();
-      if (lane == 0) red_add_release_u32(ydone + b, 1u);
     } else {
       // ---------------- x-task: complex lines ti*LPW + h (rows; real: row pairs)
-      int ok = 1;
       if (lane == 0) {
         long long polls = 0;
         while (ld_acquire_u32(ydone + b) < (unsigned)NY) {
@@ -339,45 +338,71 @@ __global__ void __launch_bounds__(FUSED_THREADS, fused_minb(LF)) k_fused2d(PassG
       ok = __shfl_sync(FULL, ok, 0);
       __syncwarp();   // every lane's reads of T_y come after lane 0's acquire
       const int line = ti * LPW + h;
-      const int row0 = CPLX ? line : 2 * line;
-      const long long ib = (long long)b * M;
-      const long long rb = ib + (long long)row0 * n0 + j;
+      row0 = CPLX ? line : 2 * line;
+      ib = (long long)b * M;
+      rb = ib + (long long)row0 * n0 + j;
+      // the input: the trial point written by this launch's y-tasks (step
+      // on load), else read-only data
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) {
+        if constexpr (CPLX) {
+          const long long e = rb + TPL * s;
+          V a = yst ? __ldcg(xin + e) : __ldg(xin + e);
+          if (xsub) a = a - __ldg(xsub + e);
+          v[s] = a;
+        } else {
+          const long long e = rb + TPL * s;
+          T a = yst ? __ldcg(xin + e) : __ldg(xin + e);
+          T c = yst ? __ldcg(xin + e + n0) : __ldg(xin + e + n0);
+          if (xsub) {
+            a -= __ldg(xsub + e);
+            c -= __ldg(xsub + e + n0);
+          }
+          v[s].x = a;
+          v[s].y = c;
+        }
+      }
+      // the epilogue needs the input again: kept in this lane's stash slots
+      C* stash = stb + (warp * LPW + h) * FFT::P;
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) stash[j + TPL * s] = v[s];
+      sym.c2 = gx.c2;
+      sym.dl = gx.dlam;
+      sym.c1c = (CPLX && gx.rcoord) ? gx.c1 * gx.rcoord[row0] : T(0);
+    }
+    // ---------------- the line operator: forward DFT, symbol and conjugation,
+    // forward DFT, conjugation (the inverse DFT of symbol x spectrum)
+    {
+      const C* tw = kind == 0 ? twy : twx;
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        FFT::forward(v, ex, tw, j);
+        if (pass == 0) {
+#pragma unroll
+          for (int s = 0; s < PPT; ++s) {
+            const T sy = sym(j + s * TPL);
+            v[s].x = sy * v[s].x;
+            v[s].y = -sy * v[s].y;
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) v[s].y = -v[s].y;
+    }
+    if (kind == 0) {
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) tyc[cb + (long long)(j + TPL * s) * n0c] = v[s];
+      __syncwarp();
+      if (lane == 0) red_add_release_u32(ydone + b, 1u);
+      continue;
+    }
+    {
       A acc[NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) acc_zero(acc[q]);
       T amax = T(0);
       if (ok) {
-        C v[PPT];
-        // the input: the trial point written by this launch's y-tasks (step
-        // on load), else read-only data
-#pragma unroll
-        for (int s = 0; s < PPT; ++s) {
-          if constexpr (CPLX) {
-            const long long e = rb + TPL * s;
-            V a = yst ? __ldcg(xin + e) : __ldg(xin + e);
-            if (xsub) a = a - __ldg(xsub + e);
-            v[s] = a;
-          } else {
-            const long long e = rb + TPL * s;
-            T a = yst ? __ldcg(xin + e) : __ldg(xin + e);
-            T c = yst ? __ldcg(xin + e + n0) : __ldg(xin + e + n0);
-            if (xsub) {
-              a -= __ldg(xsub + e);
-              c -= __ldg(xsub + e + n0);
-            }
-            v[s].x = a;
-            v[s].y = c;
-          }
-        }
-        // the epilogue needs the input again: kept in this lane's stash slots
-        C* stash = stb + (warp * LPW + h) * FFT::P;
-#pragma unroll
-        for (int s = 0; s < PPT; ++s) stash[j + TPL * s] = v[s];
-        FusedSym<T, F> sym;
-        sym.c2 = gx.c2;
-        sym.dl = gx.dlam;
-        sym.c1c = (CPLX && gx.rcoord) ? gx.c1 * gx.rcoord[row0] : T(0);
-        FFT::apply(v, ex, twx, j, sym);
+        const C* stash = stb + (warp * LPW + h) * FFT::P;
         // + T_y of the row(s): all these loads precede the epilogue's stores
 #pragma unroll
         for (int s = 0; s < PPT; ++s) {

@@ -46,7 +46,7 @@ GridHost grid_coarsen(const GridHost& g, int levels_down);
 int tuned_waves(int axis, int prec64, int cplx, int n0, int n1, int nbatch);
 void set_tuned_waves(int prec64, int cplx, int n0, int n1, int nbatch, int wx, int wy);
 // Fused 2D operator kernel or two line kernels for a float32 square grid n x n
-// (default without a measurement: fused for batches of >= 16 real fields, n <= 256).
+// (default without a measurement: fused for batches of >= 16 instances, n <= 256).
 bool tuned_fused(int cplx, int n, int nbatch);
 void set_tuned_fused(int cplx, int n, int nbatch, int on);
 // gpe_set_operator_path: 0 automatic (measured or default choice), 1 the fused

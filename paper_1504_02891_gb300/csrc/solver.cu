@@ -1319,6 +1319,24 @@ static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh
   s = Ld->create(g);
   if (s == GPE_OK) s = Lf->create(g);
   if (s != GPE_OK) return s;
+  // the refinement captures CUDA graphs, which the caller's stream may not
+  // allow (the legacy default stream cannot be captured): it runs on a
+  // private stream, after the work queued so far and before anything queued
+  // on the caller's stream later
+  struct PrivStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ~PrivStream() {
+      if (e) cudaEventDestroy(e);
+      if (s) cudaStreamDestroy(s);
+    }
+  } ps;
+  GPE_CUDA(cudaStreamCreateWithFlags(&ps.s, cudaStreamNonBlocking));
+  GPE_CUDA(cudaEventCreateWithFlags(&ps.e, cudaEventDisableTiming));
+  GPE_CUDA(cudaEventRecord(ps.e, st));
+  GPE_CUDA(cudaStreamWaitEvent(ps.s, ps.e, 0));
+  const cudaStream_t caller = st;
+  st = ps.s;
   for (int k = 0; k < n; ++k) {
     gpe_solve_report& r = reports[B.idx[k]];
     if (r.status == GPE_ENONFINITE || r.status == GPE_OK) continue;
@@ -1346,6 +1364,9 @@ static gpe_status run_batch_group(BatchGroup& B, const std::vector<GridHost>& gh
     r.nfe += l2.nfe;
     r.ms_f64 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
   }
+  GPE_CUDA(cudaEventRecord(ps.e, st));
+  GPE_CUDA(cudaStreamWaitEvent(caller, ps.e, 0));
+  GPE_CUDA(cudaStreamSynchronize(st));
   return GPE_OK;
 }
 

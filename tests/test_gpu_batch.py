@@ -141,3 +141,19 @@ def test_batch_mixed_refinement_reports_oracle_energies():
         if p["omega"] == 0.0:
             _, E_o, _ = _oracle_ground_state(p, W.normalise(p, np.abs(W.sweep_initial(p, i))))
             assert abs(reps[i]["E"] - E_o) <= 1e-9 * E_o, (i, reps[i]["E"], E_o)
+
+
+def test_batch_refinement_on_a_grid_outside_the_cluster_engine():
+    """A 256^2 complex instance: its float64 refinement runs the subproblems
+    per launch (captured in CUDA graphs, on the library's own stream) rather
+    than in the cluster engine; the reported energy is the oracle's energy of
+    the returned state."""
+    p = next(q for q in W.batched_sweep(64) if q["n"][0] == 256)
+    t = initial([p])
+    r = G.solve_batch([p], t, max_iter=300, res_tol=1e-9, mode=1, max_outer=4)[0]
+    assert r["outer_f64"] >= 1
+    g = O.build_grid(p)
+    psi = W.normalise(p, host(t[0]))
+    E = O.energy(g, psi)
+    assert abs(E - r["E"]) <= 1e-9 * abs(E), (E, r["E"])
+    assert (r["status"] == 0) == (r["res"] <= 1e-9)
