@@ -50,26 +50,29 @@ ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5
 # SHA-256 of the kernel sources it was taken with; once any of those sources
 # changes the figure no longer describes the kernel and is reported as null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "happly_traffic.json")
-KERNEL_SOURCES = ["fused2d.cuh", "lines2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"]
+# the sources that define each implementation's kernels
+KERNEL_SOURCES = {"lines": ["lines2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"],
+                  "fused2d": ["fused2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"]}
 
 
-def kernel_sources_sha256():
+def kernel_sources_sha256(impl="lines"):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[impl]:
         with open(os.path.join(ROOT, "paper_1504_02891_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic():
-    """(bytes per apply, note) from the committed ncu record, or (None, why)."""
+def measured_traffic(impl="lines"):
+    """(bytes per apply, note) from the committed ncu record of implementation
+    impl, or (None, why)."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = json.load(open(TRAFFIC_FILE))[impl]
     except Exception:
-        return None, "no ncu traffic record"
-    if rec.get("kernel_sources_sha256") != kernel_sources_sha256():
-        return None, "kernel sources changed since the ncu traffic capture"
+        return None, f"no ncu traffic record for {impl}"
+    if rec.get("kernel_sources_sha256") != kernel_sources_sha256(impl):
+        return None, f"{impl} kernel sources changed since the ncu traffic capture"
     return float(rec["dram_bytes_per_apply"]), rec.get("capture", "")
 
 
@@ -84,6 +87,8 @@ def parse():
     ap.add_argument("--only", choices=["happly", "solve"], default=None,
                     help="profiling aid: run only the H-apply loop (3 warm-up + 10 applies) or only two "
                          "mixed solves of the workload, print a one-line summary, no JSON contract line")
+    ap.add_argument("--happly-n", type=int, choices=[64, 128, 256, 512, 1024], default=512,
+                    help="with --only happly: the grid n x n of the 64-instance complex64 batch")
     ap.add_argument("--happly-path", type=int, choices=[0, 1, 2], default=0,
                     help="with --only happly: 0 = autotuned implementation, 1 = the fused kernel, 2 = the two "
                          "line kernels (1 and 2 skip the autotuning, so the launch sequence is fixed)")
@@ -311,8 +316,8 @@ def happly_throughput(G, torch, W, peaks, reps=20):
             "frac": alg_h / (ms_h * 1e-3) / 1e9 / peak, "traffic": None,
             "kernel": "",
             "us_per_apply": ms_h * 1e3, "alg_bytes_per_apply": alg_h}
-    traffic, tnote = measured_traffic()
     fused = "512x512 nbatch 64: fused kernel" in G.autotune_report()
+    traffic, tnote = measured_traffic("fused2d" if fused else "lines")
     kern = ("k_fused2d (one persistent launch: warp-per-line FFTs, y- and x-tasks per instance)" if fused else
             "k_lines_y + k_lines_x (two register-FFT line kernels)")
     hess["kernel"] = f"Hessian-vector product (gpe_hessvec) = {kern}, same batch"
@@ -573,6 +578,7 @@ def profiling_run(args):
     G.load()
     if args.only == "happly":
         p = W.config("c4")
+        p["n"] = (args.happly_n, args.happly_n)
         plan = G.Plan(p, nbatch=64, prec=G.F32)
         if args.happly_path == 0:
             plan.autotune()

@@ -37,8 +37,9 @@ namespace gpe {
 
 constexpr int FUSED_THREADS = 128;   // 4 independent warps per CTA
 // resident CTAs per SM the register budget is sized for: 128 registers per
-// lane up to 256-point lines, 168 at 512 (32 complex values per lane), 255 at 1024
-__host__ __device__ constexpr int fused_minb(int lf) { return lf <= 8 ? 4 : (lf == 9 ? 3 : 2); }
+// lane up to 256-point lines; 255 at 512 and 1024 (32 complex values per
+// lane; measured: faster than 168 registers with three CTAs per SM)
+__host__ __device__ constexpr int fused_minb(int lf) { return lf <= 8 ? 4 : 2; }
 
 // cos(pi/16), sin(pi/16), cos(3 pi/16), sin(3 pi/16)
 #define GPE_C16 0.98078528040323044913

@@ -45,12 +45,13 @@ def test_traffic_record_is_used_only_for_the_kernels_it_measured(tmp_path, monke
     rec = tmp_path / "happly_traffic.json"
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(rec))
     assert bench.measured_traffic()[0] is None                      # no record
-    rec.write_text(json.dumps({"kernel_sources_sha256": "0" * 64, "dram_bytes_per_apply": 1.0}))
-    t, why = bench.measured_traffic()
+    rec.write_text(json.dumps({"lines": {"kernel_sources_sha256": "0" * 64, "dram_bytes_per_apply": 1.0}}))
+    t, why = bench.measured_traffic("lines")
     assert t is None and "changed" in why
-    rec.write_text(json.dumps({"kernel_sources_sha256": bench.kernel_sources_sha256(),
-                               "dram_bytes_per_apply": 6.5e8, "capture": "test"}))
-    assert bench.measured_traffic() == (6.5e8, "test")
+    rec.write_text(json.dumps({"lines": {"kernel_sources_sha256": bench.kernel_sources_sha256("lines"),
+                                         "dram_bytes_per_apply": 6.5e8, "capture": "test"}}))
+    assert bench.measured_traffic("lines") == (6.5e8, "test")
+    assert bench.measured_traffic("fused2d")[0] is None             # no record of the other kernel
 
 
 def test_fused_profile_names_group_as_operator_applications():

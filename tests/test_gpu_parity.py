@@ -232,6 +232,33 @@ def test_algorithm1_iterates_match_oracle_2d(iters):
     assert abs(rep["E"] - r.F) <= 1e-12 * abs(r.F)
 
 
+@pytest.mark.parametrize("outer", [1, 2, 4, 8])
+@pytest.mark.parametrize("delta0", [1.0, 1e-4], ids=["delta1", "delta1e-4"])
+def test_regularized_newton_outer_steps_match_oracle(outer, delta0):
+    """Device Algorithm 2 (float64) follows the oracle's outer steps: the
+    subproblem of Eq. tr-sub by Algorithm 1, the ratio of Eq. TR-ratio in
+    difference form (the device's sums against the oracle's rn_ratio_terms,
+    pinned to exact differences), the acceptance of Eq. update-X and the
+    regularisation update of Eq. tau-up.  A wrong ratio flips an accept or a
+    delta update and the states part; a small delta0 makes early steps be
+    rejected, so that branch is followed too."""
+    p = W.problem(1, (128,), (-12.0,), (12.0,), "fourier", beta=100.0)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    psi0 = W.gaussian(p)
+    r = O.regularized_newton(U, U.to_X(psi0), k_init=10, k_sub=15, delta0=delta0, max_outer=outer,
+                             delta_stop=0.0, res_tol=0.0, record=True)
+    with G.Plan(p) as plan:
+        t = G.to_device(psi0)
+        rep = plan.solve(t, method=0, mode=0, levels=1, k_init=10, k_sub=15, delta0=delta0, max_outer=outer,
+                         delta_stop=0.0, res_tol=0.0)
+        got = host(t)
+    ref = U.to_psi(r.X)
+    assert rep["outer_f64"] == outer
+    assert rel(got, ref) <= 1e-8, (rel(got, ref), [h[5] for h in r.history])
+    assert abs(rep["E"] - r.F) <= 1e-12 * abs(r.F)
+
+
 def test_algorithm1_float32_tracks_oracle():
     """Float32 Algorithm 1 (100 iterations, 2D) reaches the oracle's float64
     energy after 100 iterations to float32 accuracy."""
