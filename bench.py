@@ -446,10 +446,16 @@ def our_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def phase(name):
+        # cumulative libgpe launches at each phase boundary (stderr): where a
+        # launch-count-limited ncu capture of this command ends
+        print(f"[bench] libgpe launches after {name}: {G.kernel_launches()}", file=sys.stderr, flush=True)
+
     p = W.config("c2")
     psi0 = W.gaussian(p)
     plan = G.Plan(p, prec=G.F64)
     tune_or_note(G, plan, 3)       # measured launch shapes for the three cascade grids (untimed)
+    phase("autotuning")
     init = G.to_device(psi0)
     work = torch.empty_like(init)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -479,6 +485,7 @@ def our_arm(args):
         step(opts_mixed)
         step(opts_fp64)
     torch.cuda.synchronize()
+    phase("warm-up")
 
     clocks = ClockSampler()
     time.sleep(0.3)
@@ -490,6 +497,7 @@ def our_arm(args):
     t_fp64, reps_fp64 = timed(opts_fp64, max(3, args.steps // 2))
     barrier()
     clk = clocks.stop(gpu_index=local)
+    phase("the timed mixed and float64 solves")
 
     ms_mixed, ms_fp64 = max_over_ranks([statistics.mean(t_mixed), statistics.mean(t_fp64)], world)
 
@@ -515,9 +523,13 @@ def our_arm(args):
     prof = G.profile_summary()
     G.profile_enable(False)
     roof = roofline_from_profile(prof, peaks)
+    phase("the end-to-end and profiled solves")
     c3 = config3_times(G, torch, W)
+    phase("the 3D sine solves")
     happly = happly_throughput(G, torch, W, peaks)
+    phase("the H-apply loop")
     sweep = sweep_throughput(G, torch, W, np)
+    phase("the batched sweep")
 
     if rank != 0:
         if world > 1:
@@ -565,6 +577,7 @@ def our_arm(args):
         "profile": {k: [n, round(ms, 4)] for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]},
     }
     print(json.dumps(line), flush=True)
+    phase("the report")
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

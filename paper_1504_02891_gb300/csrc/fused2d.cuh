@@ -36,6 +36,9 @@
 namespace gpe {
 
 constexpr int FUSED_THREADS = 128;   // 4 independent warps per CTA
+#ifndef FUSED_SKEW
+#define FUSED_SKEW 2
+#endif
 // resident CTAs per SM the register budget is sized for: 128 registers per
 // lane up to 256-point lines; 255 at 512 and 1024 (32 complex values per
 // lane; measured: faster than 168 registers with three CTAs per SM)
@@ -553,7 +556,9 @@ static gpe_status launch_fused2d_t(const GridHost& g, const GridDev<T>& d, const
   const long long ntask = (long long)nb * (FA.NY + FA.NX);
   const long long wpc = FUSED_THREADS / 32;
   const int grid = (int)std::max<long long>(1, std::min<long long>((ntask + wpc - 1) / wpc, (long long)occ * nsm));
-  FA.skew = (int)std::min<long long>(nb, ((long long)grid * wpc + FA.NY - 1) / FA.NY + 1);
+  // S: about twice the warps in flight over the y-tasks per instance
+  // (measured: 64 x 256^2 complex 87 -> 76 us per apply against once)
+  FA.skew = (int)std::min<long long>(nb, (FUSED_SKEW * (long long)grid * wpc + FA.NY - 1) / FA.NY + 1);
   ProfScope ps(kernel_name("fused2d", 0, CPLX, EPI, g.M * nb), st);
   k_fused2d<T, CPLX, EPI, LF, PK><<<grid, FUSED_THREADS, smem, st>>>(d.geom[0], d.geom[1], Df, FA);
   GPE_CUDA(cudaGetLastError());
