@@ -31,7 +31,17 @@
 
 namespace gpe {
 
-constexpr int LINES_THREADS = 256;
+// Threads of the x-kernel's CTA: 256 in float32.  In float64 a CTA holds as
+// few lines as it can (64 threads, or one line of F/8 threads): the float64
+// stages run on small grids (256^2: 16 CTAs of 256 threads), and the float64
+// FMA rate of one SM is 1/64 of its float32 rate, so spreading the lines over
+// more SMs is what shortens them.  At most 128 registers per thread.
+template <typename T> __host__ __device__ constexpr int lines_x_threads(int lf) {
+  return sizeof(T) == 4 ? 256 : ((1 << lf) / 8 > 64 ? (1 << lf) / 8 : 64);
+}
+template <typename T> __host__ __device__ constexpr int lines_x_minb(int lf) {
+  return 65536 / (lines_x_threads<T>(lf) * 128);
+}
 
 template <typename T, int LF>
 struct LineFFT {
@@ -206,8 +216,11 @@ struct LineSym {
 };
 
 // Threads of the y-kernel's CTA: 512 in float32 (8 columns of 512 points, 64 B
-// row segments), 256 in float64 (register budget).
-template <typename T> __host__ __device__ constexpr int lines_y_threads() { return sizeof(T) == 4 ? 512 : 256; }
+// row segments); in float64 as few columns as a line allows, as for the
+// x-kernel.
+template <typename T> __host__ __device__ constexpr int lines_y_threads(int lf) {
+  return sizeof(T) == 4 ? 512 : lines_x_threads<T>(lf);
+}
 
 // Copy of the twiddle table e^{-2 pi i n / F} into shared memory.
 template <typename C>
@@ -221,11 +234,11 @@ __device__ __forceinline__ void load_table(C* dst, const C* src, int F) {
 // fetched (cp.async, each thread its own 8 points) while this group's
 // transforms run.
 template <typename T, bool CPLX, int LF>
-__global__ void __launch_bounds__(lines_y_threads<T>()) k_lines_y(PassGeom<T> G, PassData<T> D, int colgroups,
+__global__ void __launch_bounds__(lines_y_threads<T>(LF)) k_lines_y(PassGeom<T> G, PassData<T> D, int colgroups,
                                                                   int total) {
   using FFT = LineFFT<T, LF>;
   using C = typename FFT::C;
-  constexpr int NT = lines_y_threads<T>();
+  constexpr int NT = lines_y_threads<T>(LF);
   constexpr int TPL = FFT::TPL;
   constexpr int CW = NT / TPL;
   constexpr int F = FFT::F;
@@ -309,15 +322,15 @@ __global__ void __launch_bounds__(lines_y_threads<T>()) k_lines_y(PassGeom<T> G,
 // tile, tile + tiles_per_inst, ...; the next group's input and this group's
 // epilogue operands are fetched with cp.async (each thread its own points)
 // while the transforms run.
-// (at most 128 registers: two CTAs per SM)
+// (at most 128 registers per thread)
 template <typename T, bool CPLX, int EPI, int LF>
-__global__ void __launch_bounds__(LINES_THREADS, 2) k_lines_x(PassGeom<T> G, PassData<T> D, int tiles_per_inst,
+__global__ void __launch_bounds__(lines_x_threads<T>(LF), lines_x_minb<T>(LF)) k_lines_x(PassGeom<T> G, PassData<T> D, int tiles_per_inst,
                                                               int groups) {
   using FFT = LineFFT<T, LF>;
   using C = typename FFT::C;
   using V = typename VT<T, CPLX>::V;
   using A = typename AccT<T>::type;
-  constexpr int NT = LINES_THREADS;
+  constexpr int NT = lines_x_threads<T>(LF);
   constexpr int TPL = FFT::TPL;
   constexpr int NL = NT / TPL;
   constexpr int F = FFT::F;
@@ -456,17 +469,17 @@ static gpe_status launch_lines_x(const GridDev<T>& d, const PassData<T>& Dx, int
                                  cudaStream_t st) {
   using C = typename C2t<T>::type;
   const PassGeom<T>& gx = d.geom[0];
-  constexpr int NL = LINES_THREADS / ((1 << LF0) / 8);
+  constexpr int NTX = lines_x_threads<T>(LF0);
+  constexpr int NL = NTX / ((1 << LF0) / 8);
   constexpr int NV = CPLX ? 8 : 16;
   const size_t vsz = sizeof(T) * (CPLX ? 2 : 1);
   const size_t smem = ((size_t)(1 << LF0) + 2 * (size_t)NL * LineFFT<T, LF0>::P) * sizeof(C) +
-                      3 * (size_t)NV * LINES_THREADS * vsz + (size_t)NV * LINES_THREADS * sizeof(T);
+                      3 * (size_t)NV * NTX * vsz + (size_t)NV * NTX * sizeof(T);
   static int occ = -1;
   if (occ < 0) {
     GPE_CUDA(cudaFuncSetAttribute(k_lines_x<T, CPLX, EPI, LF0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_x<T, CPLX, EPI, LF0>, LINES_THREADS,
-                                                           smem));
+    GPE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lines_x<T, CPLX, EPI, LF0>, NTX, smem));
     if (occ < 1) occ = 1;
   }
   // a few resident waves in all (4, or the measured choice), at most the
@@ -477,7 +490,7 @@ static gpe_status launch_lines_x(const GridDev<T>& d, const PassData<T>& Dx, int
   while (tiles > 1 && (long long)tiles * nbatch > d.max_blocks) tiles = (tiles + 1) / 2;
   if ((long long)tiles * nbatch > d.max_blocks) return fail(GPE_EINVAL, "reduction scratch too small");
   ProfScope ps(kernel_name("linesx", sizeof(T) == 8, CPLX, EPI, gx.M * nbatch), st);
-  k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, LINES_THREADS, smem, st>>>(gx, Dx, tiles, groups);
+  k_lines_x<T, CPLX, EPI, LF0><<<nbatch * tiles, NTX, smem, st>>>(gx, Dx, tiles, groups);
   GPE_CUDA(cudaGetLastError());
   return GPE_OK;
 }
@@ -488,9 +501,9 @@ static gpe_status launch_lines2d_t(const GridDev<T>& d, const PassData<T>& D, in
   using C = typename C2t<T>::type;
   const PassGeom<T>& gx = d.geom[0];
   const PassGeom<T>& gy = d.geom[1];
-  constexpr int YT = lines_y_threads<T>();
+  constexpr int YT = lines_y_threads<T>(LF1);
   constexpr int CW = YT / ((1 << LF1) / 8);
-  constexpr int NL = LINES_THREADS / ((1 << LF0) / 8);
+  constexpr int NL = lines_x_threads<T>(LF0) / ((1 << LF0) / 8);
   const int n0c = CPLX ? gx.n0 : gx.n0 / 2;
   const int colgroups = n0c / CW;
   const int lines = CPLX ? gx.n1 : gx.n1 / 2;
@@ -535,7 +548,7 @@ static bool lines2d_ok(const GridHost& g) {
   const int n0 = g.ext[0], n1 = g.ext[1];
   auto pow2 = [](int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; };
   if (!pow2(n0) || !pow2(n1)) return false;
-  const int cw = (sizeof(T) == 4 ? 512 : 256) / (n1 / 8), nl = LINES_THREADS / (n0 / 8);
+  const int cw = lines_y_threads<T>(ilog2(n1)) / (n1 / 8), nl = lines_x_threads<T>(ilog2(n0)) / (n0 / 8);
   const int n0c = g.is_complex ? n0 : n0 / 2;
   const int lines = g.is_complex ? n1 : n1 / 2;
   return n0c % cw == 0 && lines % nl == 0;
