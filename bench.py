@@ -51,7 +51,7 @@ ALG_REALS_PER_POINT = {"grad": 2, "hess": 3, "F": 4, "W": 4, "ratio": 3, "WS": 5
 # changes the figure no longer describes the kernel and is reported as null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "happly_traffic.json")
 # the sources that define each implementation's kernels
-KERNEL_SOURCES = {"lines": ["lines2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"],
+KERNEL_SOURCES = {"lines": ["lines2d.cuh", "linefft.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"],
                   "fused2d": ["fused2d.cuh", "ops_impl.cuh", "ops_launch.cuh", "gpe_kernels.cuh"]}
 
 

@@ -18,11 +18,17 @@
 //   7. cluster barrier; every CTA folds the CS partials in rank order and runs
 //      the step-size control (alg1_control) on its own copy of the control
 //      block -- identical inputs, identical state, no further barrier.
+// Square grids of 64, 128 and 256 points per side (LF = log2 n > 0) hold each
+// line in registers (the line FFT of the 2D line kernels: F/8 threads per
+// line, 8 points each, exchanges within the line's warp), so the line passes
+// wait at no CTA barrier; other grids stage lines through shared memory
+// (Stockham stages with a CTA barrier each, LF = 0).
 // Nothing goes to global memory until the run ends.  Cluster barriers are
 // hardware barriers; every CTA executes the same sequence of them because the
 // control decisions are bit-identical across the cluster.
 #include <cooperative_groups.h>
 #include "ops_impl.cuh"
+#include "linefft.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -40,7 +46,18 @@ namespace gpe {
 // the step is D' = (a - 1) X^k + a D + b G^ with a - 1 formed without
 // cancellation.  The objective is the model decrease
 // Re<P_k, D> + theta_k Re<X^k, D> + 1/2 Re<D, H_k D> + delta/2 ||D||^2.
-template <bool CPLX, bool SHIFT>
+// Register line FFT of the cluster engine for a square grid of 2^LF points per
+// side, or 0 (shared-memory stages).
+__host__ __device__ constexpr int cluster_lf(int n0, int n1) {
+  return (n0 == n1 && (n0 == 64 || n0 == 128 || n0 == 256)) ? (n0 == 64 ? 6 : (n0 == 128 ? 7 : 8)) : 0;
+}
+// Complex values of one exchange buffer of the register path (every line the
+// CTA's threads hold at once, row pitch of the line FFT).
+template <int LF> __host__ __device__ constexpr int cluster_exbuf() {
+  return (NTHREADS / ((1 << LF) / 8)) * LineFFT<float, LF>::P;
+}
+
+template <bool CPLX, bool SHIFT, int LF>
 __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
   using V = typename VT<float, CPLX>::V;
   using C = float2;
@@ -66,8 +83,9 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
   for (int i = 0; i < NVEC; ++i) vec[i] = reinterpret_cast<V*>(vb + (size_t)i * A.vec_bytes);  // X0 X1 G0 G1 K [Xk Pk]
   float* Vs = reinterpret_cast<float*>(vb + (size_t)NVEC * A.vec_bytes);      // potential of the local rows
   C* f0 = reinterpret_cast<C*>(vb + (size_t)NVEC * A.vec_bytes + A.vpot_bytes);
-  C* f1 = f0 + A.lch * Pm;
-  double* part = reinterpret_cast<double*>(f1 + A.lch * Pm);
+  const int fbuf = LF > 0 ? cluster_exbuf<(LF > 0 ? LF : 6)>() : A.lch * Pm;
+  C* f1 = f0 + fbuf;
+  double* part = reinterpret_cast<double*>(f1 + fbuf);
   __shared__ Alg1Ctl s_ctl;
   __shared__ double s_res[NQ];
   __shared__ float2 s_gath[16 * NQ];   // every CTA's partials, pushed by their owners
@@ -75,6 +93,26 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
 
   for (int i = tid; i < n0; i += nt) tw0[i] = A.tw0[i];
   for (int i = tid; i < n1; i += nt) tw1[i] = A.tw1[i];
+  // register path: one line transform object (square grid: both axes share
+  // the twiddle table), threads tid / TPL of a line, lane jq within it
+  using RFFT = LineFFT<float, (LF > 0 ? LF : 6)>;
+  constexpr int RTPL = RFFT::TPL, RLPC = NTHREADS / RTPL;
+  const int lq = tid / RTPL, jq = tid & (RTPL - 1);
+  RFFT rfft;
+  int rpar = 0;
+  // Storage index of element (local row r, column c) of a vector.  The
+  // register path's y-lines read one column from 32 rows per warp access; with
+  // rows n0 words apart those would all fall into one bank, so a row's
+  // columns are XOR-permuted by its row bits (pairs of real columns stay
+  // adjacent).  Elementwise phases see the same permutation in every vector.
+  auto sidx = [&](int r, int c) -> int {
+    if constexpr (LF > 0) return r * n0 + (c ^ (CPLX ? (r & 15) : 2 * (r & 15)));
+    return r * n0 + c;
+  };
+  if constexpr (LF > 0) {
+    __syncthreads();
+    rfft.init(jq, tw0);
+  }
 
   const int nloc = R * n0;                 // local elements per vector
   auto stamp = [&](int inst, int loop, int k) {
@@ -100,13 +138,14 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
     __syncthreads();
     for (int i = tid; i < nloc; i += nt) {
       if constexpr (SHIFT) {
+        const int si = sidx(i >> A.logn0, i & (n0 - 1));
         vec[s_ctl.trial][i] = vzero<V>();           // D = 0: the trial point is X^k
-        vec[5][i] = reinterpret_cast<const V*>(A.xk)[gbase + i];
-        vec[6][i] = reinterpret_cast<const V*>(A.pk)[gbase + i];
+        vec[5][si] = reinterpret_cast<const V*>(A.xk)[gbase + i];
+        vec[6][si] = reinterpret_cast<const V*>(A.pk)[gbase + i];
       } else {
-        vec[s_ctl.trial][i] = xin[i];
+        vec[s_ctl.trial][sidx(i >> A.logn0, i & (n0 - 1))] = xin[i];
       }
-      Vs[i] = Vp[i];
+      Vs[sidx(i >> A.logn0, i & (n0 - 1))] = Vp[i];
     }
     __syncthreads();
 
@@ -134,7 +173,45 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       stamp(inst, loop, 1);
       // 2. x-lines of the local rows -> K
-      {
+      if constexpr (LF > 0) {
+        const int nlines = CPLX ? R : R / 2;
+        const float c1 = om / n0;
+        LineSym<float, RFFT::F> sym;
+        sym.c2 = 0.5f / n0;
+        sym.dl = A.dlam0;
+        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
+        for (int lb = 0; lb < nlines; lb += RLPC) {
+          // every lane of a warp runs the transform (its exchanges are warp
+          // barriers); lines past the CTA's rows carry zeros and store nothing
+          const int line = lb + lq;
+          const bool act = line < nlines;
+          C v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int m = jq + s * RTPL;
+            v[s] = make_float2(0.f, 0.f);
+            if (act) {
+              if constexpr (CPLX) v[s] = Xt[sidx(line, m)];
+              else v[s] = make_float2(Xt[sidx(2 * line, m)], Xt[sidx(2 * line + 1, m)]);
+            }
+          }
+          sym.c1c = (CPLX && act) ? c1 * A.yn[rank * R + line] : 0.f;
+          ex.sync();   // the rows are rewritten only after every lane has read them
+          rfft.apply(v, ex, rpar, sym);
+          if (act) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const int m = jq + s * RTPL;
+              if constexpr (CPLX) {
+                K[sidx(line, m)] = v[s];
+              } else {
+                K[sidx(2 * line, m)] = v[s].x;
+                K[sidx(2 * line + 1, m)] = v[s].y;
+              }
+            }
+          }
+        }
+      } else {
         const int nlines = CPLX ? R : R / 2;
         const float c2 = 0.5f / n0, c1 = om / n0, dl = A.dlam0;
         for (int c0 = 0; c0 < nlines; c0 += A.lch) {
@@ -181,7 +258,53 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       cl.sync();
       stamp(inst, loop, 3);
       // 4. y-lines of this CTA's columns: gather from every CTA, add T_y Y into the owners' K
-      {
+      if constexpr (LF > 0) {
+        const int nlines = CPLX ? Cc : Cc / 2;
+        const int colbase = rank * Cc;
+        const float c1 = -om / n1;
+        // Point p of every line of this CTA is row p + rank R (mod n1): T_y is
+        // circulant along a line (a diagonal symbol on the periodic grid), so
+        // transforming the rotated line and writing back at the rotated rows
+        // gives T_y itself, and at each register slot the CTAs of the cluster
+        // read and write distinct owners instead of all the same two.
+        const int ysh = rank * R;
+        LineSym<float, RFFT::F> sym;
+        sym.c2 = 0.5f / n1;
+        sym.dl = A.dlam1;
+        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
+        for (int lb = 0; lb < nlines; lb += RLPC) {
+          const int line = lb + lq;
+          const bool act = line < nlines;
+          // column `line` (complex) or the column pair 2 line, 2 line + 1 (real)
+          const int col = CPLX ? colbase + line : colbase + 2 * line;
+          C v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int y = (jq + s * RTPL + ysh) & (n1 - 1);
+            v[s] = make_float2(0.f, 0.f);
+            if (act) {
+              const V* rem = cl.map_shared_rank(Xt, y >> logR);
+              v[s] = *reinterpret_cast<const C*>(rem + sidx(y & (R - 1), col));
+            }
+          }
+          sym.c1c = (CPLX && act) ? c1 * A.xn[col] : 0.f;
+          ex.sync();
+          rfft.apply(v, ex, rpar, sym);
+          if (act) {
+            // one writer per element; the batch's loads precede its stores
+            C* pk[8];
+            C old[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const int y = (jq + s * RTPL + ysh) & (n1 - 1);
+              pk[s] = reinterpret_cast<C*>(cl.map_shared_rank(K, y >> logR) + sidx(y & (R - 1), col));
+              old[s] = *pk[s];
+            }
+#pragma unroll
+            for (int s = 0; s < 8; ++s) *pk[s] = make_float2(old[s].x + v[s].x, old[s].y + v[s].y);
+          }
+        }
+      } else {
         const int nlines = CPLX ? Cc : Cc / 2;
         const float c2 = 0.5f / n1, c1 = -om / n1, dl = A.dlam1;
         for (int c0 = 0; c0 < nlines; c0 += A.lch) {
@@ -345,8 +468,9 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       const V* Xc = vec[s_ctl.cur];
       const V* Gc = vec[2 + s_ctl.cur];
       for (int i = tid; i < nloc; i += nt) {
-        xo[i] = Xc[i];
-        if (go) go[i] = Gc[i];
+        const int si = sidx(i >> A.logn0, i & (n0 - 1));
+        xo[i] = Xc[si];
+        if (go) go[i] = Gc[si];
       }
       if (rank == 0 && tid == 0) A.ctl[inst] = s_ctl;
       if (rank == 0 && tid < NQ) A.results[(size_t)inst * NQ + tid] = s_res[tid];
@@ -358,7 +482,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
 // Cluster size, chunk and shared memory for an n0 x n1 grid; false if the
 // state does not fit in a 16-CTA cluster.
 bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs_out, int* lch_out, int* P0, int* P1, size_t* smem_out,
-                   unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share) {
+                   unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share, int* lf_out) {
   const size_t vsz = cplx ? 8 : 4;
   const size_t total = (size_t)n0 * n1 * vsz;
   // smallest cluster whose per-CTA share of a vector is <= share (more CTAs
@@ -381,12 +505,23 @@ bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs_out, int* lch_out
   const int p0 = n0 + n0 / 16 + 1, p1 = n1 + n1 / 16 + 1;
   const size_t vb = ((size_t)R * n0 * vsz + 15) & ~(size_t)15;
   const size_t vp = ((size_t)R * n0 * 4 + 15) & ~(size_t)15;
+  // the register path (square 64^2 ... 256^2) when its exchange rows fit
+  // (up to 220 KiB of the 227 KiB a CTA may have), else the shared-memory
+  // stages with lc lines per chunk (up to 200 KiB)
+  int lf = cluster_lf(n0, n1);
   auto need = [&](int lc) {
-    return (size_t)(n0 + n1) * 8 + nvec * vb + vp + 2 * (size_t)lc * std::max(p0, p1) * 8 + NQ * 8;
+    const size_t fb = lf == 6   ? (size_t)cluster_exbuf<6>()
+                      : lf == 7 ? (size_t)cluster_exbuf<7>()
+                      : lf == 8 ? (size_t)cluster_exbuf<8>()
+                                : (size_t)lc * std::max(p0, p1);
+    return (size_t)(n0 + n1) * 8 + nvec * vb + vp + 2 * fb * 8 + NQ * 8;
   };
-  while (lch > 1 && need(lch) > 200 * 1024) lch /= 2;
+  if (lf > 0 && need(lch) > 220 * 1024) lf = 0;
+  if (lf == 0)
+    while (lch > 1 && need(lch) > 200 * 1024) lch /= 2;
   const size_t smem = need(lch);
-  if (smem > 200 * 1024) return false;
+  if (smem > (lf > 0 ? 220 : 200) * 1024) return false;
+  if (lf_out) *lf_out = lf;
   *cs_out = cs;
   *lch_out = lch;
   *P0 = p0;
@@ -395,6 +530,16 @@ bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs_out, int* lch_out
   *vec_bytes = (unsigned int)vb;
   *vpot_bytes = (unsigned int)vp;
   return true;
+}
+
+template <bool CPLX, bool SHIFT>
+static const void* cluster_fn(int lf) {
+  switch (lf) {
+    case 6: return (const void*)k_cluster_alg1<CPLX, SHIFT, 6>;
+    case 7: return (const void*)k_cluster_alg1<CPLX, SHIFT, 7>;
+    case 8: return (const void*)k_cluster_alg1<CPLX, SHIFT, 8>;
+  }
+  return (const void*)k_cluster_alg1<CPLX, SHIFT, 0>;
 }
 
 static int ilog2i(int v) {
@@ -410,8 +555,9 @@ gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st) {
   int cs, lch, P0, P1;
   size_t smem;
   unsigned int vb, vp;
+  int lf = 0;
   if (!cluster_shape(A.n0, A.n1, cplx, A.shifted ? 7 : 5, &cs, &lch, &P0, &P1, &smem, &vb, &vp,
-                     (size_t)(A.share_kb > 0 ? A.share_kb : 16) * 1024))
+                     (size_t)(A.share_kb > 0 ? A.share_kb : 16) * 1024, &lf))
     return fail(GPE_EINVAL, "grid too large for the cluster engine");
   A.cs = cs;
   A.logcs = ilog2i(cs);
@@ -422,8 +568,8 @@ gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st) {
   A.P1 = P1;
   A.vec_bytes = vb;
   A.vpot_bytes = vp;
-  const void* fn = A.shifted ? (cplx ? (const void*)k_cluster_alg1<true, true> : (const void*)k_cluster_alg1<false, true>)
-                             : (cplx ? (const void*)k_cluster_alg1<true, false> : (const void*)k_cluster_alg1<false, false>);
+  const void* fn = A.shifted ? (cplx ? cluster_fn<true, true>(lf) : cluster_fn<false, true>(lf))
+                             : (cplx ? cluster_fn<true, false>(lf) : cluster_fn<false, false>(lf));
   GPE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (cs > 8) GPE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
@@ -444,13 +590,8 @@ gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st) {
   const int ncl = std::min(A.ninst, maxc);
   cfg.gridDim = dim3(cs * ncl);
   ProfScope ps(kernel_name("cluster_alg1", 0, cplx, -1, (long long)A.n0 * A.n1), st);
-  if (A.shifted) {
-    if (cplx) GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<true, true>, A));
-    else GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<false, true>, A));
-  } else {
-    if (cplx) GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<true, false>, A));
-    else GPE_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_alg1<false, false>, A));
-  }
+  void* args[] = {&A};
+  GPE_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
   return GPE_OK;
 }
 

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, fused_minb(LF)) k_fused2d(PassG
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           if (q == Q_MAX) {
-            float m = (float)sqrt((double)amax);
+            float m = sqrtf(amax);   // correctly rounded: the float64 root rounded to float32
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(FULL, m, o));
             if (lane == 0) reinterpret_cast<float2*>(part)[q] = make_float2(ok ? m : __int_as_float(0x7fc00000), 0.f);
           } else if (q < D.nq) {

@@ -142,8 +142,10 @@ unsigned long long* persist_debug_buffer(int* n);
 void persist_debug_report(cudaStream_t st, long long M, int f64);
 
 gpe_status launch_cluster_alg1(ClusterArgs A, int cplx, cudaStream_t st);
+// lf (optional): the line path the shape uses, log2 n of the register line
+// FFT or 0 (shared-memory stages).
 bool cluster_shape(int n0, int n1, int cplx, int nvec, int* cs, int* lch, int* P0, int* P1, size_t* smem,
-                   unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share = 16 * 1024);
+                   unsigned int* vec_bytes, unsigned int* vpot_bytes, size_t share = 16 * 1024, int* lf = nullptr);
 
 void destroy_solver_cache(void* cache);
 

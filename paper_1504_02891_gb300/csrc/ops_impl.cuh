@@ -354,7 +354,12 @@ __device__ __forceinline__ void df_max(DF& a, const DF& b) { a.hi = fmaxf(a.hi, 
 // Ends with a barrier.
 template <typename A, typename M>
 static __device__ void block_partial(A (&acc)[NQ], M amax2, int nq, double* out) {
-  const double acc_max = sqrt((double)amax2);   // amax2 is the largest |.|^2 of the CTA's points
+  // amax2 is the largest |.|^2 of the CTA's points; a float32 run takes the
+  // root in float32 (correctly rounded, the same value as the float64 root
+  // rounded to float32; a float64 root costs ~0.3 us and the FP64 pipe)
+  constexpr bool F32ACC = sizeof(A) == sizeof(DF) && !std::is_same<A, double>::value;
+  const double acc_max = F32ACC ? 0.0 : sqrt((double)amax2);
+  const float acc_max_f = F32ACC ? sqrtf((float)amax2) : 0.f;
   __shared__ A red[NTHREADS / 32][NQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
@@ -362,8 +367,8 @@ static __device__ void block_partial(A (&acc)[NQ], M amax2, int nq, double* out)
   for (int q = 0; q < NQ; ++q) {
     A v;
     if (q == Q_MAX) {
-      if constexpr (sizeof(A) == sizeof(DF) && !std::is_same<A, double>::value) {
-        v.hi = (float)acc_max;
+      if constexpr (F32ACC) {
+        v.hi = acc_max_f;
         v.lo = 0.f;
         for (int o = 16; o > 0; o >>= 1) v.hi = fmaxf(v.hi, __shfl_down_sync(0xffffffffu, v.hi, o));
       } else {
