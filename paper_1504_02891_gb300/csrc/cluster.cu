@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
   const int fbuf = LF > 0 ? cluster_exbuf<(LF > 0 ? LF : 6)>() : A.lch * Pm;
   C* f1 = f0 + fbuf;
   double* part = reinterpret_cast<double*>(f1 + fbuf);
-  __shared__ Alg1Ctl s_ctl;
+  // the control block in float32 storage (its arithmetic is float32 anyway):
+  // the one-thread control then needs no float64 conversion
+  __shared__ Alg1CtlT<float> s_ctl;
   __shared__ double s_res[NQ];
   __shared__ float2 s_gath[16 * NQ];   // every CTA's partials, pushed by their owners
   using Acc = DF;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
     if (A.dbg && blockIdx.x == 0 && tid == 0 && inst == 0 && loop < A.dbg_n) {
       unsigned long long t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      A.dbg[loop * 8 + k] = t;
+      A.dbg[loop * 16 + k] = t;
     }
   };
   __shared__ int s_inst;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
     const V* xin = reinterpret_cast<const V*>(A.x) + gbase;
     const float* Vp = A.V + inst * A.vstride + (long long)rank * nloc;
     const float om = A.omega ? A.omega[inst] : 0.f;
-    if (tid == 0) s_ctl = A.ctl[inst];
+    if (tid == 0) ctl_copy(s_ctl, A.ctl[inst]);
     __syncthreads();
     for (int i = tid; i < nloc; i += nt) {
       if constexpr (SHIFT) {
@@ -172,8 +174,61 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         __syncthreads();
       }
       stamp(inst, loop, 1);
-      // 2. x-lines of the local rows -> K
       if constexpr (LF > 0) {
+        // register path: y-lines first (they gather the trial rows of every
+        // CTA, so the barrier comes first) writing K = T_y at the owners,
+        // then the x-lines add T_x to the local rows
+        cl.sync();
+        stamp(inst, loop, 2);
+        // 2. y-lines of this CTA's columns: gather from every CTA, T_y Y into the owners' K
+        {
+        const int nlines = CPLX ? Cc : Cc / 2;
+        const int colbase = rank * Cc;
+        const float c1 = -om / n1;
+        // Point p of every line of this CTA is row p + rank R (mod n1): T_y is
+        // circulant along a line (a diagonal symbol on the periodic grid), so
+        // transforming the rotated line and writing back at the rotated rows
+        // gives T_y itself, and at each register slot the CTAs of the cluster
+        // read and write distinct owners instead of all the same two.
+        const int ysh = rank * R;
+        LineSym<float, RFFT::F> sym;
+        sym.c2 = 0.5f / n1;
+        sym.dl = A.dlam1;
+        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
+        for (int lb = 0; lb < nlines; lb += RLPC) {
+          const int line = lb + lq;
+          const bool act = line < nlines;
+          // column `line` (complex) or the column pair 2 line, 2 line + 1 (real)
+          const int col = CPLX ? colbase + line : colbase + 2 * line;
+          C v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int y = (jq + s * RTPL + ysh) & (n1 - 1);
+            v[s] = make_float2(0.f, 0.f);
+            if (act) {
+              const V* rem = cl.map_shared_rank(Xt, y >> logR);
+              v[s] = *reinterpret_cast<const C*>(rem + sidx(y & (R - 1), col));
+            }
+          }
+          sym.c1c = (CPLX && act) ? c1 * A.xn[col] : 0.f;
+          ex.sync();
+          rfft.apply(v, ex, rpar, sym);
+          if (act) {
+            // K = T_y at the owners (plain remote stores; the x-lines add T_x
+            // after the barrier)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const int y = (jq + s * RTPL + ysh) & (n1 - 1);
+              *reinterpret_cast<C*>(cl.map_shared_rank(K, y >> logR) + sidx(y & (R - 1), col)) = v[s];
+            }
+          }
+        }
+        }
+        stamp(inst, loop, 3);
+        cl.sync();
+        stamp(inst, loop, 4);
+        // 4. x-lines of the local rows: K += T_x Y
+        {
         const int nlines = CPLX ? R : R / 2;
         const float c1 = om / n0;
         LineSym<float, RFFT::F> sym;
@@ -203,15 +258,19 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
             for (int s = 0; s < 8; ++s) {
               const int m = jq + s * RTPL;
               if constexpr (CPLX) {
-                K[sidx(line, m)] = v[s];
+                K[sidx(line, m)] = K[sidx(line, m)] + v[s];
               } else {
-                K[sidx(2 * line, m)] = v[s].x;
-                K[sidx(2 * line + 1, m)] = v[s].y;
+                K[sidx(2 * line, m)] += v[s].x;
+                K[sidx(2 * line + 1, m)] += v[s].y;
               }
             }
           }
         }
+        }
+        __syncthreads();
+        stamp(inst, loop, 5);
       } else {
+      {
         const int nlines = CPLX ? R : R / 2;
         const float c2 = 0.5f / n0, c1 = om / n0, dl = A.dlam0;
         for (int c0 = 0; c0 < nlines; c0 += A.lch) {
@@ -257,54 +316,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       stamp(inst, loop, 2);
       cl.sync();
       stamp(inst, loop, 3);
-      // 4. y-lines of this CTA's columns: gather from every CTA, add T_y Y into the owners' K
-      if constexpr (LF > 0) {
-        const int nlines = CPLX ? Cc : Cc / 2;
-        const int colbase = rank * Cc;
-        const float c1 = -om / n1;
-        // Point p of every line of this CTA is row p + rank R (mod n1): T_y is
-        // circulant along a line (a diagonal symbol on the periodic grid), so
-        // transforming the rotated line and writing back at the rotated rows
-        // gives T_y itself, and at each register slot the CTAs of the cluster
-        // read and write distinct owners instead of all the same two.
-        const int ysh = rank * R;
-        LineSym<float, RFFT::F> sym;
-        sym.c2 = 0.5f / n1;
-        sym.dl = A.dlam1;
-        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
-        for (int lb = 0; lb < nlines; lb += RLPC) {
-          const int line = lb + lq;
-          const bool act = line < nlines;
-          // column `line` (complex) or the column pair 2 line, 2 line + 1 (real)
-          const int col = CPLX ? colbase + line : colbase + 2 * line;
-          C v[8];
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const int y = (jq + s * RTPL + ysh) & (n1 - 1);
-            v[s] = make_float2(0.f, 0.f);
-            if (act) {
-              const V* rem = cl.map_shared_rank(Xt, y >> logR);
-              v[s] = *reinterpret_cast<const C*>(rem + sidx(y & (R - 1), col));
-            }
-          }
-          sym.c1c = (CPLX && act) ? c1 * A.xn[col] : 0.f;
-          ex.sync();
-          rfft.apply(v, ex, rpar, sym);
-          if (act) {
-            // one writer per element; the batch's loads precede its stores
-            C* pk[8];
-            C old[8];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const int y = (jq + s * RTPL + ysh) & (n1 - 1);
-              pk[s] = reinterpret_cast<C*>(cl.map_shared_rank(K, y >> logR) + sidx(y & (R - 1), col));
-              old[s] = *pk[s];
-            }
-#pragma unroll
-            for (int s = 0; s < 8; ++s) *pk[s] = make_float2(old[s].x + v[s].x, old[s].y + v[s].y);
-          }
-        }
-      } else {
+      {
         const int nlines = CPLX ? Cc : Cc / 2;
         const float c2 = 0.5f / n1, c1 = -om / n1, dl = A.dlam1;
         for (int c0 = 0; c0 < nlines; c0 += A.lch) {
@@ -354,6 +366,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       stamp(inst, loop, 4);
       cl.sync();
       stamp(inst, loop, 5);
+      }
       // 6. epilogue on the local rows
       Acc acc[NQ];
 #pragma unroll
@@ -427,8 +440,10 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
           if (++npart == 8) merge();
         }
       }
+      stamp(inst, loop, 8);
       merge();
       block_partial(acc, amax, NQ, part);
+      stamp(inst, loop, 9);
       // push this CTA's partials into every CTA's gather array (remote stores
       // do not wait; the barrier below makes them visible), so that the fold
       // reads local shared memory only.  The previous iteration's reads of
@@ -441,22 +456,32 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       stamp(inst, loop, 6);
       cl.sync();
-      // 7. fold the cluster's partials in rank order, then the control on the local copy
-      if (tid < NQ) {
-        const int q = tid;
+      stamp(inst, loop, 10);
+      // 7. fold the cluster's partials (a fixed shuffle tree over the ranks:
+      // warp w folds quantities 2w and 2w + 1, one half-warp each; every CTA
+      // folds the same values in the same order), then the control on the
+      // local copy
+      static_assert(2 * (NTHREADS / 32) >= NQ, "two quantities per warp");
+      {
+        const int lane = tid & 31, q = 2 * (tid >> 5) + (lane >> 4), r = lane & 15;
         DF v;
         acc_zero(v);
-        for (int r = 0; r < cs; ++r) {
+        if (q < NQ && r < cs) {
           const float2 f = s_gath[r * NQ + q];
+          v.hi = f.x;
+          v.lo = f.y;
+        }
+        for (int o = 8; o > 0; o >>= 1) {
           DF w;
-          w.hi = f.x;
-          w.lo = f.y;
+          w.hi = __shfl_down_sync(0xffffffffu, v.hi, o, 16);
+          w.lo = __shfl_down_sync(0xffffffffu, v.lo, o, 16);
           if (q == Q_MAX) v.hi = fmaxf(v.hi, w.hi);
           else acc_merge(v, w);
         }
-        s_res[q] = acc_value(v);
+        if (r == 0 && q < NQ) s_res[q] = acc_value(v);
       }
       __syncthreads();
+      stamp(inst, loop, 11);
       if (tid == 0) alg1_control<float>(&s_ctl, s_res);
       __syncthreads();
       stamp(inst, loop, 7);
@@ -472,7 +497,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         xo[i] = Xc[si];
         if (go) go[i] = Gc[si];
       }
-      if (rank == 0 && tid == 0) A.ctl[inst] = s_ctl;
+      if (rank == 0 && tid == 0) ctl_copy(A.ctl[inst], s_ctl);
       if (rank == 0 && tid < NQ) A.results[(size_t)inst * NQ + tid] = s_res[tid];
     }
     cl.sync();   // no CTA reuses or leaves its shared memory while others may read it

@@ -54,30 +54,96 @@ enum Epi { EPI_ACC = 0, EPI_GRAD = 1, EPI_HESS = 2, EPI_F = 3, EPI_W = 4, EPI_RA
 // Device-resident state of one Algorithm 1 run (one instance).  The passes read
 // the slot indices and scalars at their start; the last CTA of the final pass
 // updates them (see alg1_control).
-struct Alg1Ctl {
+// S: storage type of the real-valued fields (double in global memory; the
+// cluster engine's float32 runs keep a float copy in shared memory, whose
+// control then runs without float64 conversions).  The objective values stay
+// double (reported, never tested).
+template <typename S>
+struct Alg1CtlT {
   // configuration (host-written before the run)
   double alpha;        // beta / (2 h_vol)
-  double delta;        // W objective: regularisation delta^(k)
-  double rho1, eta, delta_bt, eps0, res_tol, res_rel, tau0, renorm_tol;
+  S delta;             // W objective: regularisation delta^(k)
+  S rho1, eta, delta_bt, eps0, res_tol, res_rel, tau0, renorm_tol;
   int max_bt, max_iter, objective, always_renorm;
   // slot state
   int cur, prev, trial, has_cur, done, status, phase, pad0;
-  double theta_c;      // theta of the current point (used by the passes)
-  double theta_hint;   // before the first point is accepted: a nearby theta
+  S theta_c;           // theta of the current point (used by the passes)
+  S theta_hint;        // before the first point is accepted: a nearby theta
                        // (the projected-gradient norm is formed relative to it)
   // iteration state
   int k, m, nfe, accepted_last;
-  double tau, Cg, Q, F_cur, nX, XG, GG, PP, smax, obj_last, tau_last;   // Cg = C - F_cur
-  double a, b, s;      // Cayley step coefficients of the next trial
-  double am1;          // a - 1 without cancellation (shifted subproblem form)
-  double theta_ref;    // shifted form: theta_k of the outer iterate
-  double res;          // ||A(X)X||_2 of the current point
-  double best_res;     // smallest res seen (stagnation test)
+  S tau, Cg, Q;        // Cg = C - F_cur
+  double F_cur;
+  S nX, XG, GG, PP, smax;
+  double obj_last;
+  S tau_last;
+  S a, b, s;           // Cayley step coefficients of the next trial
+  S am1;               // a - 1 without cancellation (shifted subproblem form)
+  S theta_ref;         // shifted form: theta_k of the outer iterate
+  S res;               // ||A(X)X||_2 of the current point
+  S best_res;          // smallest res seen (stagnation test)
   int k_best, stall_iters;   // stop after stall_iters accepted steps without a new best (0 = off)
   int two_slots;       // 1: slots cur/trial swap on acceptance (no third slot)
   int monotone;        // 1: monotone Armijo search, tau = alpha_hat delta_bt^m, C = F(X_cur)
-  double alpha_hat;    // first trial step of every monotone search
+  S alpha_hat;         // first trial step of every monotone search
 };
+using Alg1Ctl = Alg1CtlT<double>;
+
+// Field-by-field copy between storage types.
+template <typename D, typename S>
+__host__ __device__ inline void ctl_copy(Alg1CtlT<D>& d, const Alg1CtlT<S>& s) {
+  d.alpha = s.alpha;
+  d.delta = (D)s.delta;
+  d.rho1 = (D)s.rho1;
+  d.eta = (D)s.eta;
+  d.delta_bt = (D)s.delta_bt;
+  d.eps0 = (D)s.eps0;
+  d.res_tol = (D)s.res_tol;
+  d.res_rel = (D)s.res_rel;
+  d.tau0 = (D)s.tau0;
+  d.renorm_tol = (D)s.renorm_tol;
+  d.max_bt = s.max_bt;
+  d.max_iter = s.max_iter;
+  d.objective = s.objective;
+  d.always_renorm = s.always_renorm;
+  d.cur = s.cur;
+  d.prev = s.prev;
+  d.trial = s.trial;
+  d.has_cur = s.has_cur;
+  d.done = s.done;
+  d.status = s.status;
+  d.phase = s.phase;
+  d.pad0 = s.pad0;
+  d.theta_c = (D)s.theta_c;
+  d.theta_hint = (D)s.theta_hint;
+  d.k = s.k;
+  d.m = s.m;
+  d.nfe = s.nfe;
+  d.accepted_last = s.accepted_last;
+  d.tau = (D)s.tau;
+  d.Cg = (D)s.Cg;
+  d.Q = (D)s.Q;
+  d.F_cur = s.F_cur;
+  d.nX = (D)s.nX;
+  d.XG = (D)s.XG;
+  d.GG = (D)s.GG;
+  d.PP = (D)s.PP;
+  d.smax = (D)s.smax;
+  d.obj_last = s.obj_last;
+  d.tau_last = (D)s.tau_last;
+  d.a = (D)s.a;
+  d.b = (D)s.b;
+  d.s = (D)s.s;
+  d.am1 = (D)s.am1;
+  d.theta_ref = (D)s.theta_ref;
+  d.res = (D)s.res;
+  d.best_res = (D)s.best_res;
+  d.k_best = s.k_best;
+  d.stall_iters = s.stall_iters;
+  d.two_slots = s.two_slots;
+  d.monotone = s.monotone;
+  d.alpha_hat = (D)s.alpha_hat;
+}
 
 // Outer state of Algorithm 2 (ratio test), written by the ratio pass.
 struct RNCtl {

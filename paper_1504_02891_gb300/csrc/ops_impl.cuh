@@ -577,8 +577,8 @@ static __device__ bool grid_barrier(unsigned int* bar, int* err, long long max_p
 
 // Cayley coefficients of Theorem 3.3 for the current point and step tau, with
 // the §4 renormalisation folded in as the scale s.
-template <typename R>
-static __device__ __forceinline__ void set_coef(Alg1Ctl* c) {
+template <typename R, typename CT>
+static __device__ __forceinline__ void set_coef(CT* c) {
   const R t = (R)c->tau, nX = (R)c->nX, XG = (R)c->XG, GG = (R)c->GG, PP = (R)c->PP;
   const R nxpp = nX * PP;                            // nX*GG - XG^2, cancellation-free
   R a, b, am1;
@@ -618,8 +618,8 @@ static __device__ __forceinline__ void set_coef(Alg1Ctl* c) {
 // and the next Barzilai-Borwein step of Eq. bb-1 (alternating tau^{k,1} on even
 // k and tau^{k,2} on odd k, clamped), then the coefficients of the next trial.
 // The objective value itself is kept in float64 (reported, never tested).
-template <typename R>
-static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const double* r) {
+template <typename R, typename CT>
+static __device__ __forceinline__ void alg1_control_impl(CT* c, const double* r) {
   const double obj = (c->objective == 0) ? r[Q_E2] + c->alpha * r[Q_E4] : r[Q_E2] + r[Q_WX];
   const R nY = (R)r[Q_NY], YG = (R)r[Q_YG];
   c->obj_last = obj;
@@ -730,9 +730,9 @@ static __device__ __forceinline__ void alg1_control_impl(Alg1Ctl* c, const doubl
 // The control on a register copy of the block and of the sums: the fields are
 // read and written back once instead of one dependent shared- or global-memory
 // access per use (the control is a single thread's serial chain).
-template <typename R>
-static __device__ void alg1_control(Alg1Ctl* cp, const double* rp) {
-  Alg1Ctl c = *cp;
+template <typename R, typename CT>
+static __device__ void alg1_control(CT* cp, const double* rp) {
+  CT c = *cp;
   double r[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) r[q] = rp[q];

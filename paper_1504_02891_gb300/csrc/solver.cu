@@ -178,18 +178,25 @@ static void cluster_debug_report(cudaStream_t st, int nloops) {
   if (!g_pdbg) return;
   cudaMemcpyAsync(g_pdbg_h, g_pdbg, sizeof(unsigned long long) * 4 * PDBG_N, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  // stamp slots in time order (the kernel's slot numbers)
+  static const int order[12] = {0, 1, 2, 3, 4, 5, 8, 9, 6, 10, 11, 7};
+  // line passes: x, barrier, y, barrier (shared-memory stages) or barrier, y,
+  // barrier, x (register line FFTs)
+  static const char* name[11] = {"step", "lines1", "lines2", "lines3", "lines4", "points", "block-sum", "push",
+                                 "sync", "fold", "ctl"};
+  double s[11] = {0};
   int n = 0;
   for (int i = 0; i < nloops; ++i) {
-    const unsigned long long* t = g_pdbg_h + 8 * i;
+    const unsigned long long* t = g_pdbg_h + 16 * i;
     if (!t[0] || !t[7]) break;
-    for (int k = 0; k < 7; ++k) s[k] += (double)(t[k + 1] - t[k]);
+    for (int k = 0; k < 11; ++k) s[k] += (double)(t[order[k + 1]] - t[order[k]]);
     ++n;
   }
-  if (n)
-    fprintf(stderr, "[gpe] cluster phases (us, %d loops): step %.2f  x %.2f  sync %.2f  y %.2f  sync %.2f  epi %.2f  "
-            "sync+fold+ctl %.2f\n", n, s[0] / n / 1e3, s[1] / n / 1e3, s[2] / n / 1e3, s[3] / n / 1e3, s[4] / n / 1e3,
-            s[5] / n / 1e3, s[6] / n / 1e3);
+  if (n) {
+    fprintf(stderr, "[gpe] cluster phases (us, %d loops):", n);
+    for (int k = 0; k < 11; ++k) fprintf(stderr, " %s %.2f", name[k], s[k] / n / 1e3);
+    fprintf(stderr, "\n");
+  }
 }
 
 struct RunStats {
@@ -620,7 +627,7 @@ static gpe_status fg_run_cluster(Level<float>& L, const SolveParams& P, bool sto
   A.ctl = L.ctl;
   A.results = L.sc.results;
   A.dbg = persist_debug_buffer(&A.dbg_n);
-  if (A.dbg) A.dbg_n = A.dbg_n / 2;     // 8 stamps per loop in a buffer of 4 x n
+  if (A.dbg) A.dbg_n = A.dbg_n / 4;     // 16 stamp slots per loop in a buffer of 4 x n
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (trace_on()) {
     cudaEventCreate(&e0);
