@@ -7,22 +7,26 @@
 // its rows in shared memory: each CTA owns n1/CS consecutive rows.  Per
 // Algorithm 1 iteration:
 //   1. Cayley step on the local rows (Theorem 3.3 coefficients);
-//   2. x-lines (local rows): FFT, line symbol, inverse FFT -> K = T_x Y;
+//   2. x-lines (local rows): FFT, line symbol, inverse FFT -> T_x Y;
 //   3. cluster barrier;
 //   4. y-lines (n0/CS columns per CTA): gather the columns of Y from every
-//      CTA's shared memory (DSMEM), FFT, symbol, inverse FFT, add T_y Y into
-//      the owners' K (DSMEM read-modify-write, one writer per element);
+//      CTA's shared memory (DSMEM), FFT, symbol, inverse FFT -> T_y Y at the
+//      owners of the rows;
 //   5. cluster barrier;
-//   6. epilogue on the local rows (G = 2(K + V Y) + 4 alpha |Y|^2 Y and the
-//      float64 reduction terms, float pairs per thread), CTA partials;
-//   7. cluster barrier; every CTA folds the CS partials in rank order and runs
-//      the step-size control (alg1_control) on its own copy of the control
-//      block -- identical inputs, identical state, no further barrier.
+//   6. epilogue on the local rows (G = 2(T_x Y + T_y Y + V Y) + 4 alpha |Y|^2 Y
+//      and the float64 reduction terms, float pairs per thread), CTA partials;
+//   7. cluster barrier; every CTA folds the CS partials (a fixed shuffle tree
+//      over the ranks) and runs the step-size control (alg1_control) on its
+//      own copy of the control block -- identical inputs, identical state, no
+//      further barrier.
 // Square grids of 64, 128 and 256 points per side (LF = log2 n > 0) hold each
 // line in registers (the line FFT of the 2D line kernels: F/8 threads per
 // line, 8 points each, exchanges within the line's warp), so the line passes
-// wait at no CTA barrier; other grids stage lines through shared memory
-// (Stockham stages with a CTA barrier each, LF = 0).
+// wait at no CTA barrier: T_x goes into the trial slot's G (dead until the
+// epilogue overwrites it), T_y is stored into the owners' K with plain remote
+// stores.  Other grids stage lines through shared memory (Stockham stages
+// with a CTA barrier each, LF = 0), K = T_x and the y-lines add T_y into the
+// owners' K (remote read-modify-write, one writer per element).
 // Nothing goes to global memory until the run ends.  Cluster barriers are
 // hardware barriers; every CTA executes the same sequence of them because the
 // control decisions are bit-identical across the cluster.
@@ -33,8 +37,6 @@
 namespace cg = cooperative_groups;
 
 namespace gpe {
-
-
 
 // SHIFT = true: Algorithm 1 on the regularized Newton model W^(k) in
 // difference form.  The unknown is D = X - X^k, the gradient is kept as
@@ -175,12 +177,55 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       stamp(inst, loop, 1);
       if constexpr (LF > 0) {
-        // register path: y-lines first (they gather the trial rows of every
-        // CTA, so the barrier comes first) writing K = T_y at the owners,
-        // then the x-lines add T_x to the local rows
-        cl.sync();
+        // register path: the x-lines (local rows) first, while the other
+        // CTAs finish their steps; the barrier; the y-lines (they gather the
+        // trial rows of every CTA) write K = T_y at the owners; the barrier.
+        // The epilogue adds T_x from G.
+        // 2. x-lines of the local rows: T_x Y into the trial slot's G (dead
+        // until the epilogue, which adds it and then overwrites it)
+        {
+        const int nlines = CPLX ? R : R / 2;
+        const float c1 = om / n0;
+        LineSym<float, RFFT::F> sym;
+        sym.c2 = 0.5f / n0;
+        sym.dl = A.dlam0;
+        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
+        for (int lb = 0; lb < nlines; lb += RLPC) {
+          // every lane of a warp runs the transform (its exchanges are warp
+          // barriers); lines past the CTA's rows carry zeros and store nothing
+          const int line = lb + lq;
+          const bool act = line < nlines;
+          C v[8];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const int m = jq + s * RTPL;
+            v[s] = make_float2(0.f, 0.f);
+            if (act) {
+              if constexpr (CPLX) v[s] = Xt[sidx(line, m)];
+              else v[s] = make_float2(Xt[sidx(2 * line, m)], Xt[sidx(2 * line + 1, m)]);
+            }
+          }
+          sym.c1c = (CPLX && act) ? c1 * A.yn[rank * R + line] : 0.f;
+          ex.sync();   // the rows are rewritten only after every lane has read them
+          rfft.apply(v, ex, rpar, sym);
+          if (act) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const int m = jq + s * RTPL;
+              if constexpr (CPLX) {
+                Gt[sidx(line, m)] = v[s];
+              } else {
+                Gt[sidx(2 * line, m)] = v[s].x;
+                Gt[sidx(2 * line + 1, m)] = v[s].y;
+              }
+            }
+          }
+        }
+        }
         stamp(inst, loop, 2);
-        // 2. y-lines of this CTA's columns: gather from every CTA, T_y Y into the owners' K
+        cl.sync();
+        stamp(inst, loop, 3);
+        // 4. y-lines of this CTA's columns: gather from every CTA, T_y Y into the owners' K
         {
         const int nlines = CPLX ? Cc : Cc / 2;
         const int colbase = rank * Cc;
@@ -214,8 +259,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
           ex.sync();
           rfft.apply(v, ex, rpar, sym);
           if (act) {
-            // K = T_y at the owners (plain remote stores; the x-lines add T_x
-            // after the barrier)
+            // K = T_y at the owners (plain remote stores)
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
               const int y = (jq + s * RTPL + ysh) & (n1 - 1);
@@ -224,50 +268,8 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
           }
         }
         }
-        stamp(inst, loop, 3);
-        cl.sync();
         stamp(inst, loop, 4);
-        // 4. x-lines of the local rows: K += T_x Y
-        {
-        const int nlines = CPLX ? R : R / 2;
-        const float c1 = om / n0;
-        LineSym<float, RFFT::F> sym;
-        sym.c2 = 0.5f / n0;
-        sym.dl = A.dlam0;
-        ExRow<C, RFFT::P> ex{f0 + lq * RFFT::P, fbuf, 1 + lq, RTPL};
-        for (int lb = 0; lb < nlines; lb += RLPC) {
-          // every lane of a warp runs the transform (its exchanges are warp
-          // barriers); lines past the CTA's rows carry zeros and store nothing
-          const int line = lb + lq;
-          const bool act = line < nlines;
-          C v[8];
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const int m = jq + s * RTPL;
-            v[s] = make_float2(0.f, 0.f);
-            if (act) {
-              if constexpr (CPLX) v[s] = Xt[sidx(line, m)];
-              else v[s] = make_float2(Xt[sidx(2 * line, m)], Xt[sidx(2 * line + 1, m)]);
-            }
-          }
-          sym.c1c = (CPLX && act) ? c1 * A.yn[rank * R + line] : 0.f;
-          ex.sync();   // the rows are rewritten only after every lane has read them
-          rfft.apply(v, ex, rpar, sym);
-          if (act) {
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const int m = jq + s * RTPL;
-              if constexpr (CPLX) {
-                K[sidx(line, m)] = K[sidx(line, m)] + v[s];
-              } else {
-                K[sidx(2 * line, m)] += v[s].x;
-                K[sidx(2 * line + 1, m)] += v[s].y;
-              }
-            }
-          }
-        }
-        }
-        __syncthreads();
+        cl.sync();
         stamp(inst, loop, 5);
       } else {
       {
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         const V* Gc = hc ? vec[2 + cur] : nullptr;
         for (int i = tid; i < nloc; i += nt) {
           const V y = Xt[i], xk = Xk[i], pk = Pk[i];
-          const V lin = K[i] + Vs[i] * y;
+          const V lin = (LF > 0 ? K[i] + Gt[i] : K[i]) + Vs[i] * y;
           const float x2 = tre(xk, xk), R = tre(xk, y);
           const V hD = 2.f * lin + (4.f * al) * (x2 * y + (2.f * R) * xk);
           const V gh = pk + hD + (de - thk) * y;
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         E.delta = 0.f;
         for (int i = tid; i < nloc; i += nt) {
           const V y = Xt[i];
-          const V lin = K[i] + Vs[i] * y;
+          const V lin = (LF > 0 ? K[i] + Gt[i] : K[i]) + Vs[i] * y;
           epilogue_point<float, CPLX, EPI_F, false>(E, i, y, lin, pacc, amax);
           if (++npart == 8) merge();
         }
