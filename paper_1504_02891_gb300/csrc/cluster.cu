@@ -48,6 +48,75 @@ namespace gpe {
 // the step is D' = (a - 1) X^k + a D + b G^ with a - 1 formed without
 // cancellation.  The objective is the model decrease
 // Re<P_k, D> + theta_k Re<X^k, D> + 1/2 Re<D, H_k D> + delta/2 ||D||^2.
+// The CTA's partial sums of the NQ quantities into out[0..NQ) (float pairs).
+// Within a warp a reduce-scatter: at offsets 16, 8, 4, 2 a lane keeps one half
+// of its quantities (chosen by its lane bit) and adds its partner's copy of
+// that half, so after four steps lane l holds quantity (l >> 1) & 15 summed
+// over the 16 lanes of its parity, and offset 1 adds the other parity: 16
+// merges and 32 shuffles per lane instead of a 5-level tree per quantity.  The
+// max-norm slot is reduced by its own shuffle tree.  Then NQ threads fold the
+// warps' sums in warp order.  Every CTA and every run folds in the same order.
+__device__ __forceinline__ void cluster_block_partial(const DF (&acc)[NQ], float amax2, double* out) {
+  static_assert(NQ <= 16, "16 reduce-scatter slots");
+  __shared__ DF red[NTHREADS / 32][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  DF v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q < NQ && q != Q_MAX) v[q] = acc[q];
+    else acc_zero(v[q]);
+  }
+#pragma unroll
+  for (int o = 16, H = 8; o >= 2; o >>= 1, H >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const DF keep = up ? v[i + H] : v[i];
+      const DF send = up ? v[i] : v[i + H];
+      DF w;
+      w.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
+      w.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
+      v[i] = keep;
+      acc_merge(v[i], w);
+    }
+  }
+  {
+    DF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v[0].hi, 1);
+    w.lo = __shfl_xor_sync(0xffffffffu, v[0].lo, 1);
+    // the two parities in a fixed order (even lane's sum first)
+    if (lane & 1) {
+      DF t = w;
+      acc_merge(t, v[0]);
+      v[0] = t;
+    } else {
+      acc_merge(v[0], w);
+    }
+  }
+  float m = sqrtf(amax2);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int q = (lane >> 1) & 15;
+  if ((lane & 1) == 0 && q < NQ) {
+    if (q == Q_MAX) {
+      red[warp][q].hi = m;
+      red[warp][q].lo = 0.f;
+    } else {
+      red[warp][q] = v[0];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int qq = threadIdx.x;
+    DF a = red[0][qq];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      if (qq == Q_MAX) a.hi = fmaxf(a.hi, red[w][qq].hi);
+      else acc_merge(a, red[w][qq]);
+    }
+    reinterpret_cast<DF*>(out)[qq] = a;
+  }
+  __syncthreads();
+}
+
 // Register line FFT of the cluster engine for a square grid of 2^LF points per
 // side, or 0 (shared-memory stages).
 __host__ __device__ constexpr int cluster_lf(int n0, int n1) {
@@ -444,7 +513,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       stamp(inst, loop, 8);
       merge();
-      block_partial(acc, amax, NQ, part);
+      cluster_block_partial(acc, amax, part);
       stamp(inst, loop, 9);
       // push this CTA's partials into every CTA's gather array (remote stores
       // do not wait; the barrier below makes them visible), so that the fold
