@@ -48,6 +48,23 @@ namespace gpe {
 // the step is D' = (a - 1) X^k + a D + b G^ with a - 1 formed without
 // cancellation.  The objective is the model decrease
 // Re<P_k, D> + theta_k Re<X^k, D> + 1/2 Re<D, H_k D> + delta/2 ||D||^2.
+// Distributed-shared-memory access by shared::cluster addresses (mapa of a
+// local shared address to the CTA of cluster rank `rank`).
+__device__ __forceinline__ unsigned dsmem_addr(const void* local, int rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 dsmem_ld2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void dsmem_st2(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // The CTA's partial sums of the NQ quantities into out[0..NQ) (float pairs).
 // Within a warp a reduce-scatter: at offsets 16, 8, 4, 2 a lane keeps one half
 // of its quantities (chosen by its lane bit) and adds its partner's copy of
@@ -320,8 +337,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
             const int y = (jq + s * RTPL + ysh) & (n1 - 1);
             v[s] = make_float2(0.f, 0.f);
             if (act) {
-              const V* rem = cl.map_shared_rank(Xt, y >> logR);
-              v[s] = *reinterpret_cast<const C*>(rem + sidx(y & (R - 1), col));
+              v[s] = dsmem_ld2(dsmem_addr(Xt + sidx(y & (R - 1), col), y >> logR));
             }
           }
           sym.c1c = (CPLX && act) ? c1 * A.xn[col] : 0.f;
@@ -332,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
               const int y = (jq + s * RTPL + ysh) & (n1 - 1);
-              *reinterpret_cast<C*>(cl.map_shared_rank(K, y >> logR) + sidx(y & (R - 1), col)) = v[s];
+              dsmem_st2(dsmem_addr(K + sidx(y & (R - 1), col), y >> logR), v[s]);
             }
           }
         }

@@ -418,11 +418,26 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
   double delta = P.delta0;
   double best_res = resk;
   int stall = 0, rejects = 0;
+  // GPE_TRACE: device time of each outer step's subproblem, ratio pass and
+  // evaluation at the accepted point (events on the solver's stream)
+  struct TraceEvents {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    TraceEvents() {
+      if (trace_on())
+        for (auto& x : e) cudaEventCreate(&x);
+    }
+    ~TraceEvents() {
+      for (auto& x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } trace_ev;
+  cudaEvent_t* tev = trace_ev.e;
   for (int outer = 0; outer < P.max_outer; ++outer) {
     if (res_tol > 0.0 && resk <= res_tol) { ls.converged = true; break; }
     if (stop_f32 && resk <= P.switch_rel * fabs(thk)) break;
     // subproblem (Eq. tr-sub) by Algorithm 1 on W^(k) from X^k
     const double sub_tol = fmax(1e-2 * resk, 1e-14);
+    if (tev[0]) cudaEventRecord(tev[0], st);
     int zc = 0;
     bool done32 = false;
     if constexpr (std::is_same<T, double>::value) {
@@ -465,6 +480,7 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
       ls.nfe += r.nfe;
       zc = L.h_ctl->cur;
     }
+    if (tev[1]) cudaEventRecord(tev[1], st);
     // ratio test (Eq. TR-ratio) and delta update (Eq. tau-up)
     RNCtl& rc = *L.h_rn;
     memset(&rc, 0, sizeof(rc));
@@ -493,6 +509,7 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
     D.control = 2;
     s = apply_op<T>(L.g, L.d, D, EPI_RATIO, L.acc, false, st);
     if (s != GPE_OK) return s;
+    if (tev[2]) cudaEventRecord(tev[2], st);
     GPE_CUDA(cudaMemcpyAsync(L.h_rn, L.rn, sizeof(RNCtl), cudaMemcpyDeviceToHost, st));
     GPE_CUDA(cudaStreamSynchronize(st));
     ls.nfe += 1;
@@ -517,6 +534,16 @@ static gpe_status rn_run(Level<T>& L, const SolveParams& P, int k_init, bool sto
       Fk = r.F;
       resk = r.res;
       thk = r.theta;
+      if (tev[3]) {
+        cudaEventRecord(tev[3], st);
+        cudaEventSynchronize(tev[3]);
+        float t1 = 0, t2 = 0, t3 = 0;
+        cudaEventElapsedTime(&t1, tev[0], tev[1]);
+        cudaEventElapsedTime(&t2, tev[1], tev[2]);
+        cudaEventElapsedTime(&t3, tev[2], tev[3]);
+        fprintf(stderr, "[gpe] rn outer %d: subproblem %.1f us, ratio pass %.1f us, evaluation %.1f us\n", outer,
+                1e3 * t1, 1e3 * t2, 1e3 * t3);
+      }
       if (!stop_f32 && dmax <= P.delta_stop) { ls.converged = true; break; }   // Eq. crit2
     } else {
       ++rejects;

@@ -356,15 +356,25 @@ def test_persistent_launch_matches_per_iteration_launches(case):
         assert r["status"] == 0
 
 
-@pytest.mark.parametrize("case", ["real128", "rot64", "rot256"])
+@pytest.mark.parametrize("case", ["real128", "rot64", "rot256", "real128x64", "rot256x128"])
 def test_cluster_engine_tracks_cta_grid_path(case):
     """The float32 cluster engine (state in distributed shared memory) follows
     the CTA-grid path's Algorithm 1 iterates to float32 accuracy, and both
-    agree with the float64 oracle after 60 iterations to float32 accuracy."""
+    agree with the float64 oracle after 60 iterations to float32 accuracy.
+    Square grids take the engine's register line FFTs, the two non-square
+    cases its shared-memory line stages."""
     if case == "real128":
         p = W.config("c2")
         p["n"] = (128, 128)
         psi0 = W.gaussian(p)
+    elif case == "real128x64":
+        p = W.problem(2, (128, 64), (-16.0, -8.0), (16.0, 8.0), "fourier", beta=400.0,
+                      potential={"kind": "harmonic", "gamma": (1.0, 2.0)})
+        psi0 = W.gaussian(p)
+    elif case == "rot256x128":
+        p = W.problem(2, (256, 128), (-16.0, -12.0), (16.0, 12.0), "fourier", beta=500.0, omega=0.6,
+                      is_complex=True, potential={"kind": "harmonic", "gamma": (1.0, 1.2)})
+        psi0 = W.rotating_initial(p, "c", noise=1e-2, seed=5)
     else:
         n = 64 if case == "rot64" else 256
         p = W.problem(2, (n, n), (-12.0, -12.0), (12.0, 12.0), "fourier", beta=500.0, omega=0.7,
@@ -388,7 +398,7 @@ def test_cluster_engine_tracks_cta_grid_path(case):
     for cluster in (0, 1):
         psi, E = outs[(400, cluster)]
         assert abs(E - O.energy(g, psi)) <= 1e-5 * abs(E), (cluster, E, O.energy(g, psi))
-    if case == "real128":
+    if case in ("real128", "real128x64"):
         # non-rotating: both runs have converged to the oracle's minimum
         r = O.feasible_gradient(U.fg, U.to_X(psi0), max_iter=400, eps0=0.0)
         for cluster in (0, 1):
