@@ -263,10 +263,13 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
       }
       stamp(inst, loop, 1);
       if constexpr (LF > 0) {
-        // register path: the x-lines (local rows) first, while the other
-        // CTAs finish their steps; the barrier; the y-lines (they gather the
-        // trial rows of every CTA) write K = T_y at the owners; the barrier.
-        // The epilogue adds T_x from G.
+        // register path: every thread arrives at the cluster barrier once
+        // its part of the trial rows is formed (release), runs the x-lines
+        // of the local rows while the other CTAs finish their steps, then
+        // waits (acquire); the y-lines (they gather the trial rows of every
+        // CTA) write K = T_y at the owners; the barrier.  The epilogue adds
+        // T_x from G.
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
         // 2. x-lines of the local rows: T_x Y into the trial slot's G (dead
         // until the epilogue, which adds it and then overwrites it)
         {
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(NTHREADS) k_cluster_alg1(ClusterArgs A) {
         }
         }
         stamp(inst, loop, 2);
-        cl.sync();
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
         stamp(inst, loop, 3);
         // 4. y-lines of this CTA's columns: gather from every CTA, T_y Y into the owners' K
         {
