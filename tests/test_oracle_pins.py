@@ -818,3 +818,26 @@ def test_armijo_steps_are_the_armijo_points():
         X = r.X
         F, G = U.fg(X)
     assert min(ms) == 0 and max(ms) >= 1, ms
+
+
+@pytest.mark.parametrize("kind,odd_axes", [("10", (1,)), ("01", (0,)), ("11", (0, 1))])
+def test_table10_parity_classes_are_invariant(kind, odd_axes):
+    """§4.4 (Table 10): the asymmetric initial data are exactly odd under the
+    reflections they name (reversing an array axis of the sine grid's
+    symmetric interior nodes) and even under the others, and the discrete
+    gradient of the energy keeps that parity, so Algorithm 1 (Cayley steps
+    of X and G) stays in the class in exact arithmetic: re-imposing the
+    parity only removes rounding (reading S33)."""
+    p = W.config("t10")
+    p["n"] = (32, 32)
+    X = W.excited_initial(p, kind)
+    for ax in (0, 1):
+        sign = -1.0 if ax in odd_axes else 1.0
+        assert np.array_equal(np.flip(X, axis=ax), sign * X), (kind, ax)
+    g = O.build_grid(p)
+    U = O.Unified(g)
+    _, G = U.fg(U.to_X(X))
+    scale = np.abs(G).max()
+    for ax in (0, 1):
+        sign = -1.0 if ax in odd_axes else 1.0
+        assert np.abs(np.flip(G, axis=ax) - sign * G).max() <= 1e-12 * scale, (kind, ax)
